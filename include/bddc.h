@@ -1,0 +1,211 @@
+/*
+ * bddc.h - C ABI of the GB300 adaptive BDDC solver for mixed RT0/P0 Darcy flow.
+ *
+ * Method: B. Sousedik, "On adaptive BDDC for the flow in heterogeneous porous
+ * media" (arXiv:1901.02090).  The library solves the saddle-point system of
+ * Sec. 4, eq. (system),
+ *     [A  B^T] [u]   [g]
+ *     [B  0  ] [p] = [f],
+ * with a(u,v) = int k^{-1} u.v, b(u,q) = -int (div u) q, <f,q> = -int f q
+ * (Sec. 2, eqs. (a), (b), (rhs)), lowest-order Raviart-Thomas fluxes and
+ * piecewise-constant pressures on a Cartesian grid, by Algorithm 1 of the
+ * paper: a coarse solve (Step 1), independent subdomain solves (Step 2), and
+ * conjugate gradients on the divergence-free correction preconditioned by
+ * BDDC (Step 3, Algorithm 2), with flux constraints selected by Algorithm 3.
+ *
+ * Data conventions (all arrays are in the caller's memory, host or device;
+ * the library detects which with cudaPointerGetAttributes and copies them):
+ *   - cells are numbered c = i + nx*(j + ny*k);
+ *   - faces are numbered axis-major (all x-faces, then y, then z); inside an
+ *     axis a face is numbered lexicographically over the grid extended by
+ *     one along that axis;
+ *   - a flux is the total normal flux through a face, positive along +axis;
+ *   - pressure is one value per cell;
+ *   - f is the source density per unit volume (positive = injection);
+ *   - bc_type has one entry per face: -1 inside the domain, 0 no-flow
+ *     boundary (zero normal flux), 1 prescribed pressure (value in
+ *     bc_value at solve time).  In 2D the grid has nz = 1 and unit thickness.
+ *   - a batch of instances is solved together: per-instance arrays are
+ *     concatenated in instance order.
+ *
+ * Errors: every function returns BDDC_OK (0) or a negative code; the text
+ * of the last error of a handle is returned by bddc_last_error.  No function
+ * aborts the process or faults the GPU on invalid input.
+ *
+ * Threading: a handle is used by one host thread at a time; all its GPU work
+ * is ordered on the stream given at setup.
+ */
+#ifndef BDDC_H
+#define BDDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BDDC_OK 0
+#define BDDC_E_INVALID_ARG (-1)   /* bad size, pointer or option */
+#define BDDC_E_PARTITION (-2)     /* empty or face-disconnected subdomain, bad ids */
+#define BDDC_E_PERM (-3)          /* permeability not finite or not positive */
+#define BDDC_E_OOM (-4)           /* device or host allocation failed */
+#define BDDC_E_NOT_CONVERGED (-5) /* maxit reached; outputs hold the last iterate */
+#define BDDC_E_BREAKDOWN (-6)     /* (r,z) <= 0 or (d,Kd) <= 0 in CG */
+#define BDDC_E_TIMEOUT (-7)       /* a device-side wait exceeded its limit */
+#define BDDC_E_CUDA (-8)          /* a CUDA runtime call failed */
+#define BDDC_E_SETUP (-9)         /* a local or coarse factorisation failed */
+
+/* Precision of the subdomain-correction operators (Algorithm 2, step 2) and
+ * of the coarse basis: FP64, or FP32 storage with FP32 arithmetic.  The
+ * operator, the CG recurrence, the inner products and the coarse solve are
+ * always FP64. */
+#define BDDC_PREC_FP64 0
+#define BDDC_PREC_FP32 1
+
+#define BDDC_SCALING_MULTIPLICITY 0
+#define BDDC_SCALING_STIFFNESS 1
+
+typedef struct {
+    int dim;      /* 2 or 3 */
+    int n[3];     /* cells per axis; n[2] == 1 in 2D */
+    double h[3];  /* cell size per axis; h[2] == 1 in 2D */
+} bddc_grid;
+
+typedef struct {
+    bddc_grid grid;
+    const double* perm;       /* n_cells * perm_ncomp, > 0; k per cell (isotropic)
+                                 or per cell and axis (diagonal tensor) */
+    int perm_ncomp;           /* 1 or dim */
+    const int32_t* partition; /* n_cells subdomain ids 0..N-1 (boxes or any
+                                 face-connected sets) */
+    const int8_t* bc_type;    /* n_faces, see above */
+} bddc_instance;
+
+typedef struct {
+    /* Algorithm 3 threshold tau: adaptive flux constraints are added on every
+     * face where the local eigenproblem (Sec. 3.1, eq.
+     * (eigenvalue-problem-local-matrix)) has eigenvalues above tau.
+     * tau <= 0 or infinite: face-average constraints only (Assumption 1). */
+    double tau;
+    int scaling;          /* BDDC_SCALING_*, weights of E (Sec. 3, Remark) */
+    int precision;        /* BDDC_PREC_* */
+    int maxit;            /* CG iteration limit (> 0) */
+    int pressure_scaling; /* 1: rescale the pressure block by D (Sec. 4) */
+    int n_threads;        /* host threads used by setup; 0 = all cores */
+} bddc_options;
+
+typedef struct {
+    int iterations;        /* CG iterations of Step 3 */
+    int status;            /* BDDC_OK, BDDC_E_NOT_CONVERGED or BDDC_E_BREAKDOWN */
+    double kappa;          /* Lanczos estimate from the CG coefficients (Sec. 5) */
+    double relres;         /* final ||r||/||r_0|| of the reduced system */
+    double omega_tilde;    /* condition indicator, eq. (indicator); 0 if none */
+    int n_subdomains;      /* N */
+    int n_interface;       /* interface flux dofs (incl. pressure faces) */
+    int n_coarse;          /* coarse dofs: flux constraints + N pressures */
+    int n_adaptive;        /* adaptive constraints added by Algorithm 3 */
+} bddc_stats;
+
+typedef struct bddc_handle bddc_handle;
+
+/* Default options: tau = 0 (face averages), multiplicity scaling, FP64,
+ * maxit = 5000, pressure scaling on, all host threads. */
+void bddc_default_options(bddc_options* opt);
+
+/* Set up one or more independent instances (Algorithm 1 setup: local
+ * matrices (Sec. 2), constraints (Sec. 4.1 eq. (C^i), Algorithm 3), local
+ * Schur complements and subdomain-correction operators (Algorithm 2), coarse
+ * basis and coarse problem).  Inputs are copied; nothing is retained.
+ * `cuda_stream` (a cudaStream_t, or NULL for the default stream) orders all
+ * later GPU work of the handle.  On success *out receives a handle that owns
+ * all device memory; on failure *out is NULL and the code says why. */
+int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* opt,
+               void* cuda_stream, bddc_handle** out);
+
+/* Solve all instances of the handle (Algorithm 1: Steps 1, 2 and 3 with the
+ * BDDC preconditioner of Algorithm 2) to relative residual tol of the
+ * reduced Step-3 system.
+ *   f         : sum n_cells, source density per cell
+ *   bc_value  : sum n_faces, pressure on bc_type == 1 faces (others ignored)
+ *   flux      : sum n_faces (out), normal flux per face (0 on no-flow faces)
+ *   pressure  : sum n_cells (out)
+ *   iterations: n_instances (out, may be NULL)
+ * Host or device pointers.  Returns BDDC_OK if every instance converged,
+ * else the first failing instance's code (outputs still written). */
+int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double tol,
+               double* flux, double* pressure, int* iterations);
+
+/* Per-instance statistics of the last solve. */
+int bddc_get_stats(const bddc_handle* h, int instance, bddc_stats* out);
+
+/* Sizes of the handle: instances, total interface dofs (the length of the
+ * vectors of bddc_apply_operator), total subdomains. */
+int bddc_sizes(const bddc_handle* h, int* n_instances, int64_t* n_interface,
+               int64_t* n_subdomains);
+
+/* The Step-3 reduced operator (Sec. 3, eqs. (corr-reduced-1/2)) on device
+ * vectors: q = S u + B_0^T p0 with S = sum_i R_i^T S^i R_i, where u has
+ * n_interface entries (interface flux dofs of all instances, each
+ * instance's dofs sorted by global face id) and p0 one entry per subdomain
+ * (subdomain pressure constants in the rescaled variables of Sec. 4).
+ * Device pointers only; ordered on the handle's stream. */
+int bddc_apply_operator(bddc_handle* h, const double* u, const double* p0, double* q);
+
+/* The BDDC preconditioner (Algorithm 2) on device vectors: residual r
+ * (n_interface) -> (z, z0), z the averaged flux correction (n_interface),
+ * z0 the coarse pressure per subdomain. */
+int bddc_apply_preconditioner(bddc_handle* h, const double* r, double* z, double* z0);
+
+/* Subassembled operator apply from caller-owned device data, the kernel of
+ * eqs. (corr-reduced-1/2) without a handle: q = sum_i R_i^T S^i R_i u.
+ *   n_sub       : number of subdomains
+ *   ng          : n_sub local interface sizes (each <= 1024)
+ *   slot_offset : n_sub + 1 prefix offsets of the local slots (sum of ng)
+ *   S_offset    : n_sub offsets (in doubles) of each S^i in S
+ *   S           : the dense symmetric S^i, row-major, ng x ng each
+ *   gidx        : slot -> global interface index
+ *   partner     : slot -> slot of the other copy of the same dof, or -1
+ *   u           : n_interface input
+ *   q           : n_interface output (every entry is written)
+ *   slot_scratch: caller-owned scratch of slot_offset[n_sub] doubles
+ * Device pointers; stream is a cudaStream_t or NULL. */
+int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset,
+                            const int64_t* S_offset, const double* S, const int* gidx,
+                            const int* partner, int64_t n_interface, const double* u,
+                            double* q, double* slot_scratch, void* stream);
+
+/* Device time (ms) of the last solve's main kernel (the persistent Step 1-3
+ * kernel), measured with CUDA events around its launch, and the algorithmic
+ * bytes it moved (matrix entries and vectors per iteration times the
+ * iterations, plus the pre- and post-processing passes). */
+int bddc_last_solve_timing(const bddc_handle* h, double* kernel_ms, double* algorithmic_bytes);
+
+/* Host-only inspection of the setup (no GPU needed): runs the same setup as
+ * bddc_setup and keeps the packed operators in host memory, so that tests
+ * and diagnostics can read them.  Arrays are exported by name:
+ *   int32 : sub_inst sub_ng sub_ni sub_nc sub_m sub_local slot_g
+ *           slot_partner cslot_c c_slot_a c_slot_b g_slot_a g_slot_b
+ *   int64 : inst_goff inst_ng inst_coff inst_ncn inst_ncf inst_kinv_off
+ *           inst_s0 inst_s1 inst_face_off inst_nfaces inst_cell_off
+ *           inst_ncells off_S off_F off_P off_Gpre off_Gpost off_slot
+ *           off_cslot off_cell off_int cell_gid int_fid g_fid
+ *   double: inst_vol inst_omega sub_d slot_w slot_dsig g_bsign S F P Gpre
+ *           Gpost Kinv  (F and P are FP64 copies even for FP32 setups)
+ * bddc_host_setup_query gives the element count and size (0 count for an
+ * unknown name); bddc_host_setup_copy copies the array into dst. */
+typedef struct bddc_host_setup bddc_host_setup;
+int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt,
+                           bddc_host_setup** out);
+int bddc_host_setup_query(const bddc_host_setup* hs, const char* name, int64_t* count, int* elem_bytes);
+int bddc_host_setup_copy(const bddc_host_setup* hs, const char* name, void* dst);
+void bddc_host_setup_destroy(bddc_host_setup* hs);
+
+const char* bddc_last_error(const bddc_handle* h);
+const char* bddc_error_string(int code);
+void bddc_destroy(bddc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_H */

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of ``libbddc.so`` (argument marshalling only).
+
+Every function mirrors a C entry point of ``include/bddc.h``; all numerical
+work happens inside the library (host setup in C++, everything per solve in
+CUDA kernels on the GPU).  Arrays may be NumPy arrays (host) or CUDA torch
+tensors (device); the library detects which.  If the shared library is
+missing this module raises on import: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbddc.so")
+
+BDDC_OK = 0
+BDDC_E_INVALID_ARG = -1
+BDDC_E_PARTITION = -2
+BDDC_E_PERM = -3
+BDDC_E_OOM = -4
+BDDC_E_NOT_CONVERGED = -5
+BDDC_E_BREAKDOWN = -6
+BDDC_E_TIMEOUT = -7
+BDDC_E_CUDA = -8
+BDDC_E_SETUP = -9
+BDDC_PREC_FP64 = 0
+BDDC_PREC_FP32 = 1
+BDDC_SCALING_MULTIPLICITY = 0
+BDDC_SCALING_STIFFNESS = 1
+
+
+class bddc_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double * 3)]
+
+
+class bddc_instance(C.Structure):
+    _fields_ = [("grid", bddc_grid), ("perm", C.c_void_p), ("perm_ncomp", C.c_int),
+                ("partition", C.c_void_p), ("bc_type", C.c_void_p)]
+
+
+class bddc_options(C.Structure):
+    _fields_ = [("tau", C.c_double), ("scaling", C.c_int), ("precision", C.c_int),
+                ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int)]
+
+
+class bddc_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("kappa", C.c_double),
+                ("relres", C.c_double), ("omega_tilde", C.c_double), ("n_subdomains", C.c_int),
+                ("n_interface", C.c_int), ("n_coarse", C.c_int), ("n_adaptive", C.c_int)]
+
+
+class BDDCError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"bddc error {code} ({error_string(code)}): {msg}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with paper_1901_02090_gb300.build.build() "
+            "(nvcc for sm_103a); there is no fallback implementation")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sigs = {
+        "bddc_default_options": (None, [P]),
+        "bddc_setup": (C.c_int, [C.c_int, P, P, P, P]),
+        "bddc_solve": (C.c_int, [P, P, P, C.c_double, P, P, P]),
+        "bddc_get_stats": (C.c_int, [P, C.c_int, P]),
+        "bddc_sizes": (C.c_int, [P, P, P, P]),
+        "bddc_apply_operator": (C.c_int, [P, P, P, P]),
+        "bddc_apply_preconditioner": (C.c_int, [P, P, P, P]),
+        "bddc_subassembled_apply": (C.c_int, [C.c_int, P, P, P, P, P, P, C.c_int64, P, P, P, P]),
+        "bddc_last_solve_timing": (C.c_int, [P, P, P]),
+        "bddc_host_setup_create": (C.c_int, [C.c_int, P, P, P]),
+        "bddc_host_setup_query": (C.c_int, [P, C.c_char_p, P, P]),
+        "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
+        "bddc_host_setup_destroy": (None, [P]),
+        "bddc_last_error": (C.c_char_p, [P]),
+        "bddc_error_string": (C.c_char_p, [C.c_int]),
+        "bddc_destroy": (None, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
+            "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
+            "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
+            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_last_error",
+            "bddc_error_string", "bddc_destroy")
+
+
+def error_string(code: int) -> str:
+    return lib.bddc_error_string(int(code)).decode()
+
+
+def default_options(**kw) -> bddc_options:
+    o = bddc_options()
+    lib.bddc_default_options(C.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "tau" and not np.isfinite(v):
+            v = 0.0
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """Data pointer of a NumPy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class _Keep:
+    """Host copies of the instance arrays that must outlive the setup call."""
+
+    def __init__(self, problems):
+        self.arrays = []
+        self.inst = (bddc_instance * len(problems))()
+        for i, pb in enumerate(problems):
+            g = pb.grid
+            perm = np.ascontiguousarray(pb.perm, dtype=np.float64)
+            part = np.ascontiguousarray(pb.partition, dtype=np.int32)
+            bct = np.ascontiguousarray(pb.bc_type, dtype=np.int8)
+            self.arrays += [perm, part, bct]
+            inst = self.inst[i]
+            inst.grid.dim = g.dim
+            for a in range(3):
+                inst.grid.n[a] = int(g.n[a])
+                inst.grid.h[a] = float(g.h[a])
+            inst.perm = perm.ctypes.data
+            inst.perm_ncomp = 1 if perm.ndim == 1 else perm.shape[1]
+            inst.partition = part.ctypes.data
+            inst.bc_type = bct.ctypes.data
+
+
+class Handle:
+    """A set-up batch of instances on the GPU (owns the C handle)."""
+
+    def __init__(self, problems, options: bddc_options, stream=None):
+        self.problems = list(problems)
+        keep = _Keep(self.problems)
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(stream))
+        rc = lib.bddc_setup(len(self.problems), keep.inst, C.byref(options), s, C.byref(h))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, lib.bddc_last_error(None).decode())
+        self._h = h
+        self.n_cells = np.array([pb.grid.n_cells for pb in self.problems], dtype=np.int64)
+        self.n_faces = np.array([len(pb.bc_type) for pb in self.problems], dtype=np.int64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bddc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def solve(self, f, bc_value, tol, flux, pressure, iterations=None, check=True):
+        rc = lib.bddc_solve(self._h, _ptr(f), _ptr(bc_value), float(tol), _ptr(flux),
+                            _ptr(pressure), _ptr(iterations))
+        if check and rc != BDDC_OK:
+            raise BDDCError(rc, lib.bddc_last_error(self._h).decode())
+        return rc
+
+    def stats(self, instance=0) -> bddc_stats:
+        st = bddc_stats()
+        rc = lib.bddc_get_stats(self._h, int(instance), C.byref(st))
+        if rc != BDDC_OK:
+            raise BDDCError(rc)
+        return st
+
+    def sizes(self):
+        ni, ng, ns = C.c_int(), C.c_int64(), C.c_int64()
+        lib.bddc_sizes(self._h, C.byref(ni), C.byref(ng), C.byref(ns))
+        return ni.value, ng.value, ns.value
+
+    def apply_operator(self, u, p0, q):
+        rc = lib.bddc_apply_operator(self._h, _ptr(u), _ptr(p0), _ptr(q))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, lib.bddc_last_error(self._h).decode())
+
+    def apply_preconditioner(self, r, z, z0):
+        rc = lib.bddc_apply_preconditioner(self._h, _ptr(r), _ptr(z), _ptr(z0))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, lib.bddc_last_error(self._h).decode())
+
+    def last_solve_timing(self):
+        ms, by = C.c_double(), C.c_double()
+        lib.bddc_last_solve_timing(self._h, C.byref(ms), C.byref(by))
+        return ms.value, by.value
+
+
+def setup(problems, options=None, stream=None) -> Handle:
+    """bddc_setup for a list of ``synth.Problem``-like objects."""
+    return Handle(problems, options if options is not None else default_options(), stream)
+
+
+def subassembled_apply(n_sub, ng, slot_offset, S_offset, S, gidx, partner, n_interface, u, q,
+                       slot_scratch, stream=None):
+    rc = lib.bddc_subassembled_apply(int(n_sub), _ptr(ng), _ptr(slot_offset), _ptr(S_offset), _ptr(S),
+                                     _ptr(gidx), _ptr(partner), int(n_interface), _ptr(u), _ptr(q),
+                                     _ptr(slot_scratch), None if stream is None else C.c_void_p(int(stream)))
+    if rc != BDDC_OK:
+        raise BDDCError(rc)
+
+
+class HostSetup:
+    """bddc_host_setup_*: the packed setup operators in host memory."""
+
+    _DT = {4: np.int32, 8: None}
+
+    def __init__(self, problems, options=None):
+        keep = _Keep(list(problems))
+        h = C.c_void_p()
+        opt = options if options is not None else default_options()
+        rc = lib.bddc_host_setup_create(len(keep.inst), keep.inst, C.byref(opt), C.byref(h))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, lib.bddc_last_error(None).decode())
+        self._h = h
+
+    _INT64 = {"inst_goff", "inst_ng", "inst_coff", "inst_ncn", "inst_ncf", "inst_kinv_off", "inst_s0",
+              "inst_s1", "inst_face_off", "inst_nfaces", "inst_cell_off", "inst_ncells", "off_S", "off_F",
+              "off_P", "off_Gpre", "off_Gpost", "off_slot", "off_cslot", "off_cell", "off_int", "cell_gid",
+              "int_fid", "g_fid"}
+
+    def get(self, name: str) -> np.ndarray:
+        n, eb = C.c_int64(), C.c_int()
+        rc = lib.bddc_host_setup_query(self._h, name.encode(), C.byref(n), C.byref(eb))
+        if rc != BDDC_OK:
+            raise KeyError(name)
+        if eb.value == 4:
+            dt = np.int32
+        elif name in self._INT64:
+            dt = np.int64
+        else:
+            dt = np.float64
+        out = np.empty(n.value, dtype=dt)
+        if n.value:
+            lib.bddc_host_setup_copy(self._h, name.encode(), out.ctypes.data)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bddc_host_setup_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,62 @@
+// Internal types shared by the host setup (bddc_setup.cpp) and the device
+// code (bddc_kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+
+namespace bddc {
+
+// Host-side result of the setup of all instances, packed for upload.
+// Every per-subdomain matrix is stored "input-major": entry (out, in) of an
+// operator is at [in * n_out + out], so that a thread per output reads
+// consecutive addresses when it walks the inputs.
+struct Packed {
+    // per instance
+    std::vector<int64_t> inst_goff, inst_ng;        // interface vector offset, size
+    std::vector<int64_t> inst_coff, inst_ncn;       // coarse vector offset, n_cf + N
+    std::vector<int64_t> inst_ncf;                  // coarse flux dofs
+    std::vector<int64_t> inst_kinv_off;             // offset of the coarse inverse
+    std::vector<int64_t> inst_s0, inst_s1;          // subdomain range
+    std::vector<int64_t> inst_face_off, inst_nfaces;
+    std::vector<int64_t> inst_cell_off, inst_ncells;
+    std::vector<double> inst_vol;
+    std::vector<int> inst_nadapt;
+    std::vector<double> inst_omega;
+    // per subdomain
+    std::vector<int> sub_inst, sub_ng, sub_ni, sub_nc, sub_m, sub_local;
+    std::vector<int64_t> off_S, off_F, off_P, off_Gpre, off_Gpost;
+    std::vector<int64_t> off_slot, off_cslot, off_cell, off_int;  // n_sub + 1
+    std::vector<double> sub_d;
+    // per local interface slot
+    std::vector<int> slot_g, slot_partner;
+    std::vector<double> slot_w, slot_dsig;
+    // per local coarse slot: instance-local coarse index
+    std::vector<int> cslot_c;
+    // per local cell / interior flux: index into the batched output arrays
+    std::vector<int64_t> cell_gid, int_fid;
+    // per global interface dof
+    std::vector<int64_t> g_fid;
+    std::vector<int> g_slot_a, g_slot_b;
+    std::vector<double> g_bsign;  // +1 pressure face on a min side, -1 max side, 0 otherwise
+    // per coarse flux dof (batched): the <= 2 coarse slots that hold it
+    std::vector<int> c_slot_a, c_slot_b;
+    // matrices
+    std::vector<double> S, F64, P64, Gpre, Gpost, Kinv;
+    std::vector<float> F32, P32;
+    int precision = BDDC_PREC_FP64;
+    int64_t n_sub = 0, n_gamma = 0, n_coarse_vec = 0;
+    int max_ng = 0, max_m = 0, max_ncn = 0, max_out_post = 0, max_in_post = 0;
+};
+
+struct SetupResult {
+    int code = BDDC_OK;
+    std::string msg;
+};
+
+SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& out);
+
+}  // namespace bddc
