@@ -1,0 +1,296 @@
+"""Benchmark: BDDC-PCG solves/s at relative residual 1e-8 on GB300.
+
+Workload (one step = one bddc_solve of a batch): the 2D 60 x 220 channelized
+field of 20 x 10 ft cells (6 x 22 subdomains of 10 x 10, log10 k from -3 to 4,
+contrast ~1e7), pressure drop along x, adaptive constraints with tau = 10,
+subdomain corrections and coarse basis in FP32 with the FP64 CG, a batch of B
+independent seeded fields solved by one persistent kernel.  Beside it the
+plain FP64 one-solve-at-a-time path is timed on the same kind of field
+(solves/s and p50/p99 latency).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDDC-PCG solves/s at rel.res 1e-8 vs plain FP64 path; p50/p99 solve latency"
+WORKLOAD = ("2D 60x220 channelized (contrast ~1e7), 6x22 subdomains of 10x10 cells, adaptive tau=10, "
+            "FP64 CG with FP32-apply subdomain corrections, batch of independent fields per step")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--tau", type=float, default=10.0)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--single-solves", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def problems(rank, batch):
+    from synth import make_config
+    return [make_config("c2", seed=2090 + rank * 100000 + i) for i in range(batch)]
+
+
+class Clocks:
+    """nvidia-smi clock sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bddc_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(tau, tol, n_solves=1):
+    """The oracle as it stands on one field of the workload (setup untimed)."""
+    from synth import make_config
+    from oracle import BDDCOracle
+    pb = make_config("c2", seed=2090)
+    o = BDDCOracle(pb, tau=tau)
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(n_solves):
+        its.append(o.solve(tol=tol).iterations)
+    dt = time.perf_counter() - t0
+    return {"value": n_solves / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_solves} solve(s) of one 60x220 channelized field (tau={tau:g}, tol={tol:g}, "
+                      f"{its[0]} CG iterations), oracle setup excluded; NumPy/SciPy FP64"}
+
+
+def run_reference(args):
+    rank, _, world = dist_info()
+    if world > 1 and rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    from synth import make_config
+    from oracle import BDDCOracle
+    pb = make_config("c2", seed=2090)
+    o = BDDCOracle(pb, tau=args.tau)
+    for _ in range(min(W, 1)):
+        o.solve(tol=args.tol)
+    t0 = time.perf_counter()
+    steps = max(1, min(K, 3))
+    for _ in range(steps):
+        o.solve(tol=args.tol)
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": min(W, 1), "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("batch of independent fields per step",
+                                                   "one field per step (CPU oracle)"), "tau": args.tau,
+                       "tol": args.tol},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "kind": "oracle", "cores": os.cpu_count(),
+                             "sample": f"{steps} solves of one field, setup excluded"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_1901_02090_gb300 import bddc
+    rank, local_rank, world = dist_info()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    K, W, B = args.steps, max(3, args.warmup), args.batch
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    # ---- batched mixed-precision path -----------------------------------------
+    pbs = problems(rank, B)
+    t0 = time.perf_counter()
+    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32), stream=sptr)
+    setup_s = time.perf_counter() - t0
+    f_h = np.ascontiguousarray(np.concatenate([pb.f for pb in pbs]))
+    bc_h = np.ascontiguousarray(np.concatenate([pb.bc_value for pb in pbs]))
+    f_d = torch.as_tensor(f_h, device=dev)
+    bc_d = torch.as_tensor(bc_h, device=dev)
+    flux = torch.empty(len(bc_h), dtype=torch.float64, device=dev)
+    pres = torch.empty(len(f_h), dtype=torch.float64, device=dev)
+    its = torch.empty(B, dtype=torch.int32, device=dev)
+    for _ in range(W):
+        rc = h.solve(f_d, bc_d, args.tol, flux, pres, its, check=False)
+        if rc != bddc.BDDC_OK:
+            bad = [(i, h.stats(i).status, h.stats(i).iterations, h.stats(i).relres) for i in range(B)
+                   if h.stats(i).status != bddc.BDDC_OK]
+            raise RuntimeError(f"batched solve failed (rc={rc}): instances {bad[:8]}")
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kbytes, iters = [], [], []
+    ev0.record(stream)
+    for _ in range(K):
+        h.solve(f_d, bc_d, args.tol, flux, pres, its)
+        ms, by = h.last_solve_timing()
+        kms.append(ms)
+        kbytes.append(by)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    iters = [h.stats(i).iterations for i in range(B)]
+    kappas = [h.stats(i).kappa for i in range(B)]
+    n_adapt = [h.stats(i).n_adaptive for i in range(B)]
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t[0])
+    value = world * B * K / (total_ms / 1e3)
+
+    # e2e through host buffers (copies inside the timed region)
+    flux_h = np.empty(len(bc_h))
+    pres_h = np.empty(len(f_h))
+    its_h = np.empty(B, dtype=np.int32)
+    h.solve(f_h, bc_h, args.tol, flux_h, pres_h, its_h)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(K):
+        h.solve(f_h, bc_h, args.tol, flux_h, pres_h, its_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    e2e_value = world * B * K / e2e_s
+    h.close()
+
+    # ---- plain FP64 one-solve-at-a-time path ------------------------------------
+    pb1 = pbs[0]
+    h1 = bddc.setup([pb1], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64), stream=sptr)
+    f1 = torch.as_tensor(pb1.f, device=dev)
+    bc1 = torch.as_tensor(pb1.bc_value, device=dev)
+    flux1 = torch.empty(len(pb1.bc_value), dtype=torch.float64, device=dev)
+    pres1 = torch.empty(pb1.grid.n_cells, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        h1.solve(f1, bc1, args.tol, flux1, pres1)
+    lat = []
+    for _ in range(args.single_solves):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h1.solve(f1, bc1, args.tol, flux1, pres1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(b))
+    single_its = h1.stats(0).iterations
+    single_kms = h1.last_solve_timing()[0]
+    h1.close()
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak()
+    avg_ms = float(np.mean(kms))
+    avg_bytes = float(np.mean(kbytes))
+    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 CG + f32 subdomain apply", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": B, "tau": args.tau, "tol": args.tol,
+                   "grid": "60x220 cells, 20x10 ft", "subdomains": "6x22 of 10x10",
+                   "l2": "operators streamed per iteration exceed L2 (inputs larger than L2)",
+                   "setup_s": round(setup_s, 2)},
+        "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
+        "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
+        "fp64_single": {"value": 1e3 / statistics.mean(lat), "unit": "solves/s", "p50_ms": p50, "p99_ms": p99,
+                        "iterations": single_its, "kernel_ms": single_kms, "solves": len(lat)},
+        "latency_batched_ms": {"p50": total_ms / K, "p99": max(kms)},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(8 * (len(f_h) + len(bc_h))),
+                "d2h_bytes_per_step": int(8 * (len(flux_h) + len(pres_h)) + 4 * B)},
+        "gpu_launches": K,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "bddc_solve_kernel<float> (persistent Steps 1-3 + post)",
+                     "kernel_ms_mean": avg_ms, "algorithmic_bytes_per_launch": avg_bytes},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.tau, args.tol)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -186,12 +186,14 @@ int bddc_last_solve_timing(const bddc_handle* h, double* kernel_ms, double* algo
  * and diagnostics can read them.  Arrays are exported by name:
  *   int32 : sub_inst sub_ng sub_ni sub_nc sub_m sub_local slot_g
  *           slot_partner cslot_c c_slot_a c_slot_b g_slot_a g_slot_b
+ *           slot_fcs cslot_n slot_fperm cslot_fstart
  *   int64 : inst_goff inst_ng inst_coff inst_ncn inst_ncf inst_kinv_off
  *           inst_s0 inst_s1 inst_face_off inst_nfaces inst_cell_off
  *           inst_ncells off_S off_F off_P off_Gpre off_Gpost off_slot
  *           off_cslot off_cell off_int cell_gid int_fid g_fid
- *   double: inst_vol inst_omega sub_d slot_w slot_dsig g_bsign S F P Gpre
- *           Gpost Kinv  (F and P are FP64 copies even for FP32 setups)
+ *   double: inst_vol inst_omega sub_d slot_w slot_dsig slot_coef g_bsign S F P Gpre
+ *           Gpost Kinv P64  (F and P are FP64 copies of the operators the
+ *           GPU applies, FP32-rounded for FP32 setups; P64 is the FP64 basis)
  * bddc_host_setup_query gives the element count and size (0 count for an
  * unknown name); bddc_host_setup_copy copies the array into dst. */
 typedef struct bddc_host_setup bddc_host_setup;
@@ -200,6 +202,13 @@ int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bdd
 int bddc_host_setup_query(const bddc_host_setup* hs, const char* name, int64_t* count, int* elem_bytes);
 int bddc_host_setup_copy(const bddc_host_setup* hs, const char* name, void* dst);
 void bddc_host_setup_destroy(bddc_host_setup* hs);
+
+/* Diagnostic copy of a device work vector of the last solve into host
+ * memory: "x" "r0" "r1" "d0" "d1" "g" "u0" (interface), "ql" "zl" "yl" "rl"
+ * "tl" (local slots), "rcl" (coarse slots), "wc" (coarse vectors), "xp" "zp"
+ * "prhs" "part_rr" "part_rz" "part_dq" (per subdomain).  *count receives
+ * the length; dst may be NULL to query it. */
+int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64_t* count);
 
 const char* bddc_last_error(const bddc_handle* h);
 const char* bddc_error_string(int code);

@@ -343,9 +343,9 @@ class BDDCOracle:
         r0 = nrm(r, rho)
         relres, alphas, betas = [1.0], [], []
         it = 0
-        if np.linalg.norm(r) > floor and rho > RHO_FLUX_CONVERGED * max(rho0, 1e-300):
-            if not rho > 0:
-                raise BreakdownError("(r, z) <= 0 at start")
+        # M is positive semi-definite, so (r, z) <= 0 at the start is a
+        # rounded zero: r lies in range(B_0^T) and only the pressure is left
+        if np.linalg.norm(r) > floor and rho > 0.0:
             d, dp = z.copy(), zp.copy()
             for k in range(maxit):
                 q, _ = self.apply_operator(d, dp)

@@ -80,6 +80,7 @@ def _load():
         "bddc_host_setup_query": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
         "bddc_host_setup_destroy": (None, [P]),
+        "bddc_debug_vector": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_last_error": (C.c_char_p, [P]),
         "bddc_error_string": (C.c_char_p, [C.c_int]),
         "bddc_destroy": (None, [P]),
@@ -95,7 +96,7 @@ lib = _load()
 EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
-            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_last_error",
+            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_last_error",
             "bddc_error_string", "bddc_destroy")
 
 
@@ -204,6 +205,15 @@ class Handle:
         rc = lib.bddc_apply_preconditioner(self._h, _ptr(r), _ptr(z), _ptr(z0))
         if rc != BDDC_OK:
             raise BDDCError(rc, lib.bddc_last_error(self._h).decode())
+
+    def debug_vector(self, name):
+        n = C.c_int64()
+        rc = lib.bddc_debug_vector(self._h, name.encode(), None, C.byref(n))
+        if rc != BDDC_OK:
+            raise KeyError(name)
+        out = np.empty(n.value)
+        lib.bddc_debug_vector(self._h, name.encode(), out.ctypes.data, None)
+        return out
 
     def last_solve_timing(self):
         ms, by = C.c_double(), C.c_double()

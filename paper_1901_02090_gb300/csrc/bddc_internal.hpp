@@ -34,6 +34,15 @@ struct Packed {
     // per local interface slot
     std::vector<int> slot_g, slot_partner;
     std::vector<double> slot_w, slot_dsig;
+    // per local interface slot: the local coarse slot of its face's net-flux
+    // row and the row's coefficient (+1/-1); per local coarse slot: the
+    // number of face dofs of a net-flux row (0 for adaptive rows)
+    std::vector<int> slot_fcs, cslot_n;
+    std::vector<double> slot_coef;
+    // per subdomain the local slots grouped by net-flux row (slot_fperm,
+    // indexed from the subdomain's slot offset) and, per local coarse slot,
+    // the start of its group (-1 for adaptive rows)
+    std::vector<int> slot_fperm, cslot_fstart;
     // per local coarse slot: instance-local coarse index
     std::vector<int> cslot_c;
     // per local cell / interior flux: index into the batched output arrays

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,47 +42,31 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ float warp_sumf(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// fixed-order block sum; `red` holds >= 16 doubles of shared memory
-__device__ double block_sum(double v, double* red) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double r = 0.0;
-        for (int i = 0; i < kThreads / 32; ++i) r += red[i];
-        red[8] = r;
-    }
-    __syncthreads();
-    const double r = red[8];
-    __syncthreads();
-    return r;
-}
-
-// fixed-order sum of part[s0..s1) by warp 0, broadcast to the block
-__device__ double range_sum(const double* part, int64_t s0, int64_t s1, double* red) {
-    if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += 32) v += __ldcg(part + s);
-        v = warp_sum(v);
-        if (threadIdx.x == 0) red[9] = v;
-    }
-    __syncthreads();
-    const double r = red[9];
-    __syncthreads();
-    return r;
-}
 
 __device__ __forceinline__ bool slot_owner(int slot, int partner) { return partner < 0 || slot < partner; }
 
+// warp-uniform read of an instance's done flag (the owner warp may set it
+// while other warps are in the same phase)
 __device__ __forceinline__ int inst_done(const Params& p, int b) {
-    return __ldcg(&p.st[b].done);
+    int f = 0;
+    if ((threadIdx.x & 31) == 0) f = __ldcg(&p.st[b].done);
+    return __shfl_sync(0xffffffffu, f, 0);
+}
+
+// block-uniform read, for the CTA-level coarse phase
+__device__ int inst_done_block(const Params& p, int b) {
+    __shared__ int flag;
+    __syncthreads();
+    if (threadIdx.x == 0) flag = __ldcg(&p.st[b].done);
+    __syncthreads();
+    return flag;
+}
+
+// fixed-order sum of part[s0..s1) by one warp (every lane gets the result)
+__device__ __forceinline__ double range_sum(const double* part, int64_t s0, int64_t s1) {
+    double v = 0.0;
+    for (int64_t s = s0 + (threadIdx.x & 31); s < s1; s += 32) v += __ldcg(part + s);
+    return warp_sum(v);
 }
 
 // grid-wide barrier with a bounded wait; false if any CTA gave up
@@ -102,7 +87,7 @@ __device__ bool grid_barrier(GridSync* gs) {
             long long spins = 0;
             while (*vgen == g0) {
                 if (++spins > kSpinLimit) { ok = 0; break; }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -114,123 +99,276 @@ __device__ bool grid_barrier(GridSync* gs) {
     return ok_sh != 0;
 }
 
-__device__ __forceinline__ void my_range(int64_t U, int64_t& a, int64_t& b) {
+// contiguous chunk of U units for this CTA / this warp
+__device__ __forceinline__ void cta_range(int64_t U, int64_t& a, int64_t& b) {
     a = (U * (int64_t)blockIdx.x) / gridDim.x;
     b = (U * ((int64_t)blockIdx.x + 1)) / gridDim.x;
 }
-
-template <class T> struct Acc;
-template <> struct Acc<double> { using type = double; };
-template <> struct Acc<float> { using type = float; };
-
-// Shared-memory layout of one CTA (dynamic): xs[max_ng] doubles,
-// xin[max_in_post] doubles, rhs[max_ncn] doubles, xsf[max_ng] floats,
-// red[16] doubles.
-struct Smem {
-    double *xs, *xin, *rhs, *red;
-    float* xsf;
-};
-__device__ __forceinline__ Smem carve(const Params& p, double* base) {
-    Smem s;
-    s.xs = base;
-    s.xin = s.xs + p.max_ng;
-    s.rhs = s.xin + p.max_in_post;
-    s.red = s.rhs + p.max_ncn;
-    s.xsf = reinterpret_cast<float*>(s.red + 16);
-    return s;
+__device__ __forceinline__ void warp_range(int64_t U, int64_t& a, int64_t& b) {
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    a = (U * w) / W;
+    b = (U * (w + 1)) / W;
 }
 
-// y_i = (sum_j M[j*n + i] * v_j), thread per output, inputs in shared memory
-template <class T, class A>
-__device__ __forceinline__ A gemv_col(const T* __restrict__ M, int n_out, int n_in, const A* v, int o) {
-    A acc = 0;
+// ---- precisions ------------------------------------------------------------------
+struct PrecFP64 {
+    using S_t = double;
+    using F_t = double;
+    static constexpr bool kMixed = false;
+};
+struct PrecMixed {
+    using S_t = double;   // the operator stays FP64: it defines the problem
+    using F_t = float;
+    static constexpr bool kMixed = true;
+};
+
+// Per-warp shared-memory slice: the staged input vector in FP64 and as an
+// FP32 pair (hi + lo), a second input vector for the Step-2 / post maps, and
+// the subdomain's coarse values.
+struct WarpSm {
+    double* x;
+    float* xh;
+    float* xl;
+    double* xin;
+    double* wcs;
+    double* tsum;  // per net-flux row sums (mixed path)
+};
+struct CtaSm {
+    double* rhs;  // staged coarse right-hand side (CTA-level)
+    WarpSm w;
+};
+__device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
+    CtaSm c;
+    c.rhs = base;
+    const int warp = threadIdx.x >> 5;
+    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1);  // in doubles
+    double* wb = base + p.max_ncn + (int64_t)warp * per_warp;
+    c.w.x = wb;
+    c.w.xh = reinterpret_cast<float*>(wb + p.max_ng);
+    c.w.xl = c.w.xh + p.max_ng;
+    c.w.xin = wb + 2 * p.max_ng;
+    c.w.wcs = c.w.xin + p.max_in_post;
+    c.w.tsum = c.w.wcs + p.max_m + 1;
+    return c;
+}
+
+// stage x[0..n) from the warp's x into the FP32 pair representation
+__device__ __forceinline__ void split_pairs(WarpSm& w, int n) {
+    for (int k = threadIdx.x & 31; k < n; k += 32) {
+        const double v = w.x[k];
+        const float h = __double2float_rn(v);
+        w.xh[k] = h;
+        w.xl[k] = __double2float_rn(v - (double)h);
+    }
+    __syncwarp();
+}
+
+// out = sum_j M[j*n_out + o] * x[j] for one output o of an input-major
+// operator; FP64 or compensated FP32-pair arithmetic
+__device__ __forceinline__ double gemv_out(const double* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
+    double a0 = 0.0, a1 = 0.0;
+    int j = 0;
 #pragma unroll 4
-    for (int j = 0; j < n_in; ++j) acc += (A)__ldg(M + (int64_t)j * n_out + o) * v[j];
+    for (; j + 1 < n_in; j += 2) {
+        a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
+        a1 = fma(__ldg(M + (int64_t)(j + 1) * n_out + o), w.x[j + 1], a1);
+    }
+    if (j < n_in) a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
+    return a0 + a1;
+}
+
+__device__ __forceinline__ double gemv_out(const float2* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
+    // (sh, sl) accumulates the products of the FP32 pairs (a.x + a.y) and
+    // (xh + xl): the exact error of a.x*xh by FMA, the two cross terms, and a
+    // Knuth two-sum of the high parts; products are rounded explicitly so
+    // that no FMA contraction merges them into the sums
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < n_in; ++j) {
+        const float2 a = __ldg(M + (int64_t)j * n_out + o);
+        const float xh = w.xh[j], xl = w.xl[j];
+        const float pr = __fmul_rn(a.x, xh);
+        float e = __fmaf_rn(a.x, xh, -pr);
+        e = __fmaf_rn(a.x, xl, e);
+        e = __fmaf_rn(a.y, xh, e);
+        const float t = __fadd_rn(sh, pr);
+        const float bp = __fsub_rn(t, sh);
+        const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(err, e));
+    }
+    return (double)sh + (double)sl;
+}
+
+// FP32 operator on the FP32 (hi) input
+__device__ __forceinline__ double gemv_out_f(const float* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
+    float a0 = 0.0f, a1 = 0.0f;
+    int j = 0;
+#pragma unroll 4
+    for (; j + 1 < n_in; j += 2) {
+        a0 = fmaf(__ldg(M + (int64_t)j * n_out + o), w.xh[j], a0);
+        a1 = fmaf(__ldg(M + (int64_t)(j + 1) * n_out + o), w.xh[j + 1], a1);
+    }
+    if (j < n_in) a0 = fmaf(__ldg(M + (int64_t)j * n_out + o), w.xh[j], a0);
+    return (double)(a0 + a1);
+}
+__device__ __forceinline__ double gemv_out_f(const double* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
+    return gemv_out(M, n_out, n_in, w, o);
+}
+
+// restriction rc_a = sum_k P[a*ng + k] x[k] (warp dot per row a)
+__device__ __forceinline__ void restrict_rows(const double* __restrict__ P, int m, int ng, const WarpSm& w, double* out) {
+    const int l = threadIdx.x & 31;
+    for (int a = 0; a < m; ++a) {
+        double acc = 0.0;
+        for (int k = l; k < ng; k += 32) acc = fma(__ldg(P + (int64_t)a * ng + k), w.x[k], acc);
+        acc = warp_sum(acc);
+        if (l == 0) out[a] = acc;
+    }
+}
+__device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m, int ng, const WarpSm& w, double* out) {
+    const int l = threadIdx.x & 31;
+    for (int a = 0; a < m; ++a) {
+        float acc = 0.0f;
+        for (int k = l; k < ng; k += 32) acc = fmaf(__ldg(P + (int64_t)a * ng + k), w.xh[k], acc);
+        const double d = warp_sum((double)acc);
+        if (l == 0) out[a] = d;
+    }
+}
+
+// prolongation value for output k: sum_a P[a*ng + k] wcs[a]
+__device__ __forceinline__ double prolong_out(const double* __restrict__ P, int m, int ng, const WarpSm& w, int k) {
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc = fma(__ldg(P + (int64_t)a * ng + k), w.wcs[a], acc);
     return acc;
 }
-
-// subdomain correction and coarse restriction of the weighted residual in
-// sm.xs: yl = F xs, rcl = Psi^T xs (Algorithm 2 steps 1-2, local parts)
-template <class T>
-__device__ void restrict_apply(const Params& p, int64_t s, Smem& sm) {
-    using A = typename Acc<T>::type;
-    const int ng = p.sub_ng[s], m = p.sub_m[s];
-    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
-    const T* F = reinterpret_cast<const T*>(p.F) + p.off_F[s];
-    const T* P = reinterpret_cast<const T*>(p.P) + p.off_P[s];
-    const A* v;
-    if constexpr (sizeof(T) == 4) {
-        for (int k = threadIdx.x; k < ng; k += kThreads) sm.xsf[k] = (float)sm.xs[k];
-        __syncthreads();
-        v = reinterpret_cast<const A*>(sm.xsf);
-    } else {
-        v = reinterpret_cast<const A*>(sm.xs);
-    }
-    for (int k = threadIdx.x; k < ng; k += kThreads) p.yl[so + k] = (double)gemv_col<T, A>(F, ng, ng, v, k);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int a = w; a < m; a += kThreads / 32) {
-        A acc = 0;
-        for (int k = l; k < ng; k += 32) acc += (A)__ldg(P + (int64_t)a * ng + k) * v[k];
-        double d = (double)acc;
-        d = warp_sum(d);
-        if (l == 0) p.rcl[co + a] = d;
-    }
-    __syncthreads();
-}
-
-// z_loc = Psi * wc_local (+ add), thread per output; wc staged in sm.rhs
-template <class T>
-__device__ __forceinline__ double prolong_one(const Params& p, int64_t s, int ng, int m, const double* wcs, int k) {
-    const T* P = reinterpret_cast<const T*>(p.P) + p.off_P[s];
-    using A = typename Acc<T>::type;
-    A acc = 0;
-    for (int a = 0; a < m; ++a) acc += (A)__ldg(P + (int64_t)a * ng + k) * (A)wcs[a];
+__device__ __forceinline__ double prolong_out(const float* __restrict__ P, int m, int ng, const WarpSm& w, int k) {
+    float acc = 0.0f;
+    for (int a = 0; a < m; ++a) acc = fmaf(__ldg(P + (int64_t)a * ng + k), (float)w.wcs[a], acc);
     return (double)acc;
 }
 
-__device__ void stage_wc(const Params& p, int64_t s, const double* wc_b, Smem& sm) {
+// Mixed path.  P_Z removes the net flux of a local vector through each face
+// (a symmetric projection); the FP32 operators are applied as P_Z F P_Z and
+// Psi_0 + P_Z Psi, where Psi_0 puts the unit net flux of a face-constraint
+// column uniformly on the face's dofs.  In exact arithmetic these equal F and
+// Psi; in rounded arithmetic restriction and prolongation stay transposes
+// and the preconditioner output keeps exact face net fluxes, so it stays
+// balanced (Sec. 3) to FP64 rounding.
+//
+// t[a] = sum over the dofs of net-flux row a of coef * v (lane per row)
+__device__ __forceinline__ void face_sums(const Params& p, int64_t s, const double* v, double* t) {
     const int m = p.sub_m[s];
-    const int64_t co = p.off_cslot[s];
-    for (int a = threadIdx.x; a < m; a += kThreads) sm.rhs[a] = __ldcg(wc_b + p.cslot_c[co + a]);
-    __syncthreads();
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        const int na = p.cslot_n[co + a];
+        double acc = 0.0;
+        if (na > 0) {
+            const int fs = p.cslot_fstart[co + a];
+            for (int q = 0; q < na; ++q) {
+                const int k = p.slot_fperm[so + fs + q];
+                acc += p.slot_coef[so + k] * v[k];
+            }
+        }
+        t[a] = acc;
+    }
+    __syncwarp();
+}
+// v <- P_Z v
+__device__ __forceinline__ void remove_face_flux(const Params& p, int64_t s, double* v, const double* t) {
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    for (int k = threadIdx.x & 31; k < ng; k += 32) {
+        const int a = p.slot_fcs[so + k];
+        v[k] -= p.slot_coef[so + k] * t[a] / (double)p.cslot_n[co + a];
+    }
+    __syncwarp();
+}
+// v <- P_Z v + Psi_0 wcs
+__device__ __forceinline__ void set_face_flux(const Params& p, int64_t s, double* v, const double* t,
+                                              const double* wcs) {
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    for (int k = threadIdx.x & 31; k < ng; k += 32) {
+        const int a = p.slot_fcs[so + k];
+        v[k] += p.slot_coef[so + k] * (wcs[a] - t[a]) / (double)p.cslot_n[co + a];
+    }
+    __syncwarp();
 }
 
-// ---- phases -------------------------------------------------------------------------
-template <class T>
-__device__ void ph_step1(const Params& p, int64_t s, Smem& sm) {
+__device__ __forceinline__ void stage_wc(const Params& p, int64_t s, const double* wc_b, WarpSm& w) {
+    const int m = p.sub_m[s];
+    const int64_t co = p.off_cslot[s];
+    for (int a = threadIdx.x & 31; a < m; a += 32) w.wcs[a] = __ldcg(wc_b + p.cslot_c[co + a]);
+    __syncwarp();
+}
+
+// subdomain correction and coarse restriction of the weighted residual in
+// w.x: yl = F x, rcl = Psi^T x (Algorithm 2 steps 1-2, local parts)
+template <class PR>
+__device__ void restrict_apply(const Params& p, int64_t s, WarpSm& w) {
+    using F_t = typename PR::F_t;
+    const int ng = p.sub_ng[s], m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const F_t* F = reinterpret_cast<const F_t*>(p.F) + p.off_F[s];
+    const F_t* P = reinterpret_cast<const F_t*>(p.P) + p.off_P[s];
+    if constexpr (PR::kMixed) {
+        // rc = Psi_0^T r + Psi^T P_Z r ; y = P_Z F P_Z r
+        face_sums(p, s, w.x, w.tsum);
+        remove_face_flux(p, s, w.x, w.tsum);
+        split_pairs(w, ng);
+        restrict_rows(P, m, ng, w, p.rcl + co);
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            for (int a = 0; a < m; ++a) {
+                const int na = p.cslot_n[co + a];
+                if (na > 0) p.rcl[co + a] += w.tsum[a] / (double)na;
+            }
+        for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = gemv_out_f(F, ng, ng, w, k);
+        __syncwarp();
+        face_sums(p, s, w.xin, w.tsum);
+        remove_face_flux(p, s, w.xin, w.tsum);
+        for (int k = threadIdx.x & 31; k < ng; k += 32) p.yl[so + k] = w.xin[k];
+    } else {
+        for (int k = threadIdx.x & 31; k < ng; k += 32) p.yl[so + k] = gemv_out_f(F, ng, ng, w, k);
+        restrict_rows(P, m, ng, w, p.rcl + co);
+    }
+    __syncwarp();
+}
+
+// ---- phases (warp per subdomain unless noted) --------------------------------------
+template <class PR>
+__device__ void ph_step1(const Params& p, int64_t s, WarpSm& w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
-    for (int k = threadIdx.x; k < ng; k += kThreads) {
+    const int l = threadIdx.x & 31;
+    for (int k = l; k < ng; k += 32) {
         const int gi = p.slot_g[so + k];
         const double sg = p.g_bsign[gi];
         const double gv = sg != 0.0 ? sg * p.bc_in[p.g_fid[gi]] : 0.0;
         if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.g[gi] = gv;
-        sm.xs[k] = p.slot_w[so + k] * gv;
+        w.x[k] = p.slot_w[so + k] * gv;
     }
-    __syncthreads();
-    using A = typename Acc<T>::type;
-    const T* P = reinterpret_cast<const T*>(p.P) + p.off_P[s];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int a = w; a < m; a += kThreads / 32) {
-        double acc = 0.0;  // Step 1 right-hand side in FP64 products
-        for (int k = l; k < ng; k += 32) acc += (double)(A)__ldg(P + (int64_t)a * ng + k) * sm.xs[k];
-        acc = warp_sum(acc);
-        if (l == 0) p.rcl[co + a] = acc;
-    }
+    __syncwarp();
+    // Step 1 right-hand side <g, E psi> with the FP64 coarse basis
+    restrict_rows(p.P64 + p.off_P[s], m, ng, w, p.rcl + co);
     double v = 0.0;
     const int64_t cb = p.off_cell[s];
-    for (int r = threadIdx.x; r < nc; r += kThreads) v += -p.f_in[p.cell_gid[cb + r]];
-    v = block_sum(v, sm.red);
-    if (threadIdx.x == 0) p.prhs[s] = p.sub_d[s] * p.inst_vol[b] * v;
-    __syncthreads();
+    for (int r = l; r < nc; r += 32) v += -p.f_in[p.cell_gid[cb + r]];
+    v = warp_sum(v);
+    if (l == 0) p.prhs[s] = p.sub_d[s] * p.inst_vol[b] * v;
+    __syncwarp();
 }
 
-// coarse solve rows: wc = Kinv * rhs (rhs flux part from coarse slots; the
-// pressure part is the Step-1 right-hand side or zero)
-__device__ void ph_coarse(const Params& p, int64_t u, bool step1, Smem& sm, int& staged) {
+// coarse solve rows (CTA per unit): wc = Kinv * rhs; rhs flux part from the
+// coarse slots, pressure part the Step-1 right-hand side or zero
+template <class PR>
+__device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, int& staged) {
+    using K_t = typename std::conditional<PR::kMixed, float2, double>::type;
     const int b = p.cunit_inst[u];
-    if (!step1 && inst_done(p, b)) return;
+    if (!step1 && inst_done_block(p, b)) return;
     const int64_t ncn = p.inst_ncn[b], ncf = p.inst_ncf[b], coff = p.inst_coff[b];
     const int64_t cfo = p.inst_cfoff[b];
     const int64_t ncols = step1 ? ncn : ncf;
@@ -245,62 +383,96 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, Smem& sm, int&
             } else {
                 v = __ldcg(p.prhs + s0 + (c - ncf));
             }
-            sm.rhs[c] = v;
+            rhs[c] = v;
         }
         __syncthreads();
         staged = b;
     }
-    const double* K = p.Kinv + p.inst_kinv_off[b];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const K_t* K = reinterpret_cast<const K_t*>(p.Kinv) + p.inst_kinv_off[b];
+    const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t r0 = p.cunit_row0[u];
     const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
-    for (int64_t row = r0 + w; row < r1; row += kThreads / 32) {
-        const double* kr = K + row * ncn;
-        double acc = 0.0;
-        for (int64_t c = l; c < ncols; c += 32) acc += __ldg(kr + c) * sm.rhs[c];
+    for (int64_t row = r0 + wi; row < r1; row += kWarps) {
+        const K_t* kr = K + row * ncn;
+        double acc;
+        if constexpr (PR::kMixed) {
+            float sh = 0.0f, sl = 0.0f;
+            for (int64_t c = l; c < ncols; c += 32) {
+                const float2 a = __ldg(kr + c);
+                const double xv = rhs[c];
+                const float xh = __double2float_rn(xv);
+                const float xl = __double2float_rn(xv - (double)xh);
+                const float pr = __fmul_rn(a.x, xh);
+                float e = __fmaf_rn(a.x, xh, -pr);
+                e = __fmaf_rn(a.x, xl, e);
+                e = __fmaf_rn(a.y, xh, e);
+                const float t = __fadd_rn(sh, pr);
+                const float bp = __fsub_rn(t, sh);
+                const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+                sh = t;
+                sl = __fadd_rn(sl, __fadd_rn(err, e));
+            }
+            acc = (double)sh + (double)sl;
+        } else {
+            acc = 0.0;
+            for (int64_t c = l; c < ncols; c += 32) acc = fma(__ldg(kr + c), rhs[c], acc);
+        }
         acc = warp_sum(acc);
         if (l == 0) p.wc[coff + row] = acc;
     }
 }
 
-template <class T>
-__device__ void ph_u0(const Params& p, int64_t s, Smem& sm) {
+template <class PR>
+__device__ void ph_u0(const Params& p, int64_t s, WarpSm& w) {
+    using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s];
-    stage_wc(p, s, p.wc + p.inst_coff[b], sm);
-    for (int k = threadIdx.x; k < ng; k += kThreads)
-        p.tl[so + k] = p.slot_w[so + k] * prolong_one<T>(p, s, ng, m, sm.rhs, k);
-    __syncthreads();
+    stage_wc(p, s, p.wc + p.inst_coff[b], w);
+    const F_t* P = reinterpret_cast<const F_t*>(p.P) + p.off_P[s];
+    for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = prolong_out(P, m, ng, w, k);
+    __syncwarp();
+    if constexpr (PR::kMixed) {
+        face_sums(p, s, w.xin, w.tsum);
+        set_face_flux(p, s, w.xin, w.tsum, w.wcs);
+    }
+    for (int k = threadIdx.x & 31; k < ng; k += 32) p.tl[so + k] = p.slot_w[so + k] * w.xin[k];
+    __syncwarp();
 }
 
 // Step 2 local residual r_G = S u_0 + G_pre f (stored in ql)
-__device__ void ph_step2(const Params& p, int64_t s, Smem& sm) {
+template <class PR>
+__device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
+    using S_t = typename PR::S_t;
     const int ng = p.sub_ng[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], cb = p.off_cell[s];
-    for (int k = threadIdx.x; k < ng; k += kThreads) {
+    const int l = threadIdx.x & 31;
+    for (int k = l; k < ng; k += 32) {
         const int pt = p.slot_partner[so + k];
         const double u = __ldcg(p.tl + so + k) + (pt >= 0 ? __ldcg(p.tl + pt) : 0.0);
         if (slot_owner((int)(so + k), pt)) p.u0[p.slot_g[so + k]] = u;
-        sm.xin[k] = u;
+        w.x[k] = u;
     }
-    for (int r = threadIdx.x; r < nc; r += kThreads) sm.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
-    __syncthreads();
-    const double* S = p.S + p.off_S[s];
+    for (int r = l; r < nc; r += 32) w.xin[r] = p.f_in[p.cell_gid[cb + r]];
+    __syncwarp();
+    const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     const double* G = p.Gpre + p.off_Gpre[s];
-    for (int k = threadIdx.x; k < ng; k += kThreads)
-        p.ql[so + k] = gemv_col<double, double>(S, ng, ng, sm.xin, k) +
-                       gemv_col<double, double>(G, ng, nc, sm.xin + ng, k);
-    __syncthreads();
+    for (int k = l; k < ng; k += 32) {
+        double acc = gemv_out(S, ng, ng, w, k);
+        for (int r = 0; r < nc; ++r) acc = fma(__ldg(G + (int64_t)r * ng + k), w.xin[r], acc);
+        p.ql[so + k] = acc;
+    }
+    __syncwarp();
 }
 
 // f* = g - sum_i R_i^T r_G,i ; r_0 = f*, x_0 = 0 ; then restrict r_0
-template <class T>
-__device__ void ph_fstar(const Params& p, int64_t s, Smem& sm) {
+template <class PR>
+__device__ void ph_fstar(const Params& p, int64_t s, WarpSm& w) {
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
+    const int l = threadIdx.x & 31;
     double rr = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int k = threadIdx.x; k < ng; k += kThreads) {
+    for (int k = l; k < ng; k += 32) {
         const int pt = p.slot_partner[so + k];
         const int gi = p.slot_g[so + k];
         const double gv = __ldcg(p.g + gi);
@@ -314,13 +486,13 @@ __device__ void ph_fstar(const Params& p, int64_t s, Smem& sm) {
             a2 += loc * loc;
         }
         const double wr = p.slot_w[so + k] * fs;
-        sm.xs[k] = wr;
+        w.x[k] = wr;
         p.rl[so + k] = wr;
     }
-    rr = block_sum(rr, sm.red);
-    a1 = block_sum(a1, sm.red);
-    a2 = block_sum(a2, sm.red);
-    if (threadIdx.x == 0) {
+    rr = warp_sum(rr);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (l == 0) {
         p.part_rr[s] = rr;
         p.part_a1[s] = a1;
         p.part_a2[s] = a2;
@@ -328,47 +500,70 @@ __device__ void ph_fstar(const Params& p, int64_t s, Smem& sm) {
         p.dp0[s] = 0.0;
         p.dp1[s] = 0.0;
     }
-    __syncthreads();
-    restrict_apply<T>(p, s, sm);
+    __syncwarp();
+    restrict_apply<PR>(p, s, w);
 }
 
-template <class T>
-__device__ void ph_prolong(const Params& p, int64_t s, Smem& sm) {
+template <class PR>
+__device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w) {
+    using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s];
     const double* wcb = p.wc + p.inst_coff[b];
-    stage_wc(p, s, wcb, sm);
+    stage_wc(p, s, wcb, w);
+    const F_t* P = reinterpret_cast<const F_t*>(p.P) + p.off_P[s];
+    for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = prolong_out(P, m, ng, w, k);
+    __syncwarp();
+    if constexpr (PR::kMixed) {
+        face_sums(p, s, w.xin, w.tsum);
+        set_face_flux(p, s, w.xin, w.tsum, w.wcs);
+    }
+    for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] += __ldcg(p.yl + so + k);
+    __syncwarp();
     double rz = 0.0;
-    for (int k = threadIdx.x; k < ng; k += kThreads) {
-        const double z = prolong_one<T>(p, s, ng, m, sm.rhs, k) + __ldcg(p.yl + so + k);
+    for (int k = threadIdx.x & 31; k < ng; k += 32) {
+        const double z = w.xin[k];
         p.zl[so + k] = p.slot_w[so + k] * z;
         rz += __ldcg(p.rl + so + k) * z;
     }
-    rz = block_sum(rz, sm.red);
-    if (threadIdx.x == 0) {
+    rz = warp_sum(rz);
+    if ((threadIdx.x & 31) == 0) {
         p.part_rz[s] = rz;
         p.zp[s] = __ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]);
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 constexpr double kRhoFluxConverged = 1e-24;
 
+// per-warp cache of an instance's reduced scalars within one phase
+struct InstCache {
+    int b = -1;
+    double v0 = 0.0, v1 = 0.0;
+};
+
 // convergence decision, direction update and operator apply
-__device__ void ph_dirop(const Params& p, int64_t s, int k, Smem& sm) {
+template <class PR>
+__device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+    using S_t = typename PR::S_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
     const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
-    const double rr = range_sum(p.part_rr, s0, s1, sm.red);
-    const double rz = range_sum(p.part_rz, s0, s1, sm.red);
+    const int l = threadIdx.x & 31;
+    if (cache.b != b) {
+        cache.b = b;
+        cache.v0 = range_sum(p.part_rr, s0, s1);
+        cache.v1 = range_sum(p.part_rz, s0, s1);
+    }
+    const double rr = cache.v0, rz = cache.v1;
     const bool owner = (s == s0);
     const int64_t hb = (int64_t)b * (p.maxit + 1);
     double r0, floor_, rho0;
     if (k == 0) {
-        const double a1 = range_sum(p.part_a1, s0, s1, sm.red);
-        const double a2 = range_sum(p.part_a2, s0, s1, sm.red);
+        const double a1 = range_sum(p.part_a1, s0, s1);
+        const double a2 = range_sum(p.part_a2, s0, s1);
         r0 = sqrt(rr);
         floor_ = 1e-14 * (sqrt(a1) + sqrt(a2));
         rho0 = rz;
@@ -381,15 +576,17 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, Smem& sm) {
     const double relres = (k == 0) ? 1.0 : nr / r0;
     int status = -100;  // not done
     if (k == 0) {
-        if (nr <= floor_) status = BDDC_OK;
-        else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
+        // M is positive semi-definite: (r, z) <= 0 at the start is a rounded
+        // zero, i.e. r lies in range(B_0^T) and the flux is already exact
+        if (nr <= floor_ || rz <= 0.0) status = BDDC_OK;
+        else if (!(rz == rz)) status = BDDC_E_BREAKDOWN;
     } else {
         if (relres <= p.tol || nr <= floor_ || rz <= kRhoFluxConverged * rho0) status = BDDC_OK;
         else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
         else if (k >= p.maxit) status = BDDC_E_NOT_CONVERGED;
     }
     if (owner) {
-        if (threadIdx.x == 0) {
+        if (l == 0) {
             if (k == 0) {
                 p.st[b].r0 = r0;
                 p.st[b].floor = floor_;
@@ -398,9 +595,12 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, Smem& sm) {
             p.rho_hist[hb + k] = rz;
         }
         if (status != -100) {
-            // last coarse pressure correction x_p += z_p from the final residual
-            for (int64_t t = s0 + threadIdx.x; t < s1; t += kThreads) p.xp[t] = __ldcg(p.xp + t) + __ldcg(p.zp + t);
-            if (threadIdx.x == 0) {
+            // FP64 path: last coarse pressure correction x_p += z_p from the
+            // final residual (the mixed path does it in FP64 after the loop)
+            if constexpr (!PR::kMixed)
+                for (int64_t t = s0 + l; t < s1; t += 32) p.xp[t] = __ldcg(p.xp + t) + __ldcg(p.zp + t);
+            __syncwarp();
+            if (l == 0) {
                 p.st[b].status = status;
                 p.st[b].iterations = k;
                 p.st[b].relres = relres;
@@ -410,48 +610,54 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, Smem& sm) {
             }
         }
     }
+    __syncwarp();
     if (status != -100) return;
     const double beta = (k == 0) ? 0.0 : rz / __ldcg(p.rho_hist + hb + k - 1);
-    if (owner && threadIdx.x == 0) p.beta_hist[hb + k] = beta;
+    if (owner && l == 0) p.beta_hist[hb + k] = beta;
     double* dold = (k & 1) ? p.dbuf0 : p.dbuf1;
     double* dnew = (k & 1) ? p.dbuf1 : p.dbuf0;
     double* dpold = (k & 1) ? p.dp0 : p.dp1;
     double* dpnew = (k & 1) ? p.dp1 : p.dp0;
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
-    for (int kk = threadIdx.x; kk < ng; kk += kThreads) {
+    for (int kk = l; kk < ng; kk += 32) {
         const int pt = p.slot_partner[so + kk];
         const int gi = p.slot_g[so + kk];
         const double z = __ldcg(p.zl + so + kk) + (pt >= 0 ? __ldcg(p.zl + pt) : 0.0);
         const double dn = (k == 0) ? z : z + beta * __ldcg(dold + gi);
         if (slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
-        sm.xs[kk] = dn;
+        w.x[kk] = dn;
     }
     const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
-    if (threadIdx.x == 0) dpnew[s] = dpn;
-    __syncthreads();
-    const double* S = p.S + p.off_S[s];
+    if (l == 0) dpnew[s] = dpn;
+    __syncwarp();
+    const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     double dq = 0.0;
-    for (int kk = threadIdx.x; kk < ng; kk += kThreads) {
-        const double q = gemv_col<double, double>(S, ng, ng, sm.xs, kk) + p.slot_dsig[so + kk] * dpn;
+    for (int kk = l; kk < ng; kk += 32) {
+        const double q = gemv_out(S, ng, ng, w, kk) + p.slot_dsig[so + kk] * dpn;
         p.ql[so + kk] = q;
-        dq += sm.xs[kk] * q;
+        dq += w.x[kk] * q;
     }
-    dq = block_sum(dq, sm.red);
-    if (threadIdx.x == 0) p.part_dq[s] = dq;
-    __syncthreads();
+    dq = warp_sum(dq);
+    if (l == 0) p.part_dq[s] = dq;
+    __syncwarp();
 }
 
-template <class T>
-__device__ void ph_update(const Params& p, int64_t s, int k, Smem& sm) {
+template <class PR>
+__device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
     const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
     const int64_t hb = (int64_t)b * (p.maxit + 1);
-    const double dq = range_sum(p.part_dq, s0, s1, sm.red);
+    const int l = threadIdx.x & 31;
+    if (cache.b != b) {
+        cache.b = b;
+        cache.v0 = range_sum(p.part_dq, s0, s1);
+    }
+    const double dq = cache.v0;
     const bool owner = (s == s0);
     if (!(dq > 0.0)) {
-        if (owner && threadIdx.x == 0) {
+        if (owner && l == 0) {
             p.st[b].status = BDDC_E_BREAKDOWN;
             p.st[b].iterations = k;
             p.st[b].relres = -1.0;
@@ -459,10 +665,11 @@ __device__ void ph_update(const Params& p, int64_t s, int k, Smem& sm) {
             p.st[b].done = 1;
             atomicSub(p.n_active, 1);
         }
+        __syncwarp();
         return;
     }
     const double alpha = __ldcg(p.rho_hist + hb + k) / dq;
-    if (owner && threadIdx.x == 0) p.alpha_hist[hb + k] = alpha;
+    if (owner && l == 0) p.alpha_hist[hb + k] = alpha;
     const double* rold = (k & 1) ? p.rbuf1 : p.rbuf0;
     double* rnew = (k & 1) ? p.rbuf0 : p.rbuf1;
     const double* dcur = (k & 1) ? p.dbuf1 : p.dbuf0;
@@ -470,7 +677,7 @@ __device__ void ph_update(const Params& p, int64_t s, int k, Smem& sm) {
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
     double rr = 0.0;
-    for (int kk = threadIdx.x; kk < ng; kk += kThreads) {
+    for (int kk = l; kk < ng; kk += 32) {
         const int pt = p.slot_partner[so + kk];
         const int gi = p.slot_g[so + kk];
         const double q = __ldcg(p.ql + so + kk) + (pt >= 0 ? __ldcg(p.ql + pt) : 0.0);
@@ -481,102 +688,155 @@ __device__ void ph_update(const Params& p, int64_t s, int k, Smem& sm) {
             rr += rn * rn;
         }
         const double wr = p.slot_w[so + kk] * rn;
-        sm.xs[kk] = wr;
+        w.x[kk] = wr;
         p.rl[so + kk] = wr;
     }
-    rr = block_sum(rr, sm.red);
-    if (threadIdx.x == 0) {
+    rr = warp_sum(rr);
+    if (l == 0) {
         p.part_rr[s] = rr;
         p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
     }
-    __syncthreads();
-    restrict_apply<T>(p, s, sm);
+    __syncwarp();
+    restrict_apply<PR>(p, s, w);
 }
 
-__device__ void ph_post(const Params& p, int64_t s, Smem& sm) {
+// mixed path: FP64 restriction of the final residual for the closing coarse
+// pressure correction
+__device__ void ph_final_restrict(const Params& p, int64_t s, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    const int ng = p.sub_ng[s], m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const int it = __ldcg(&p.st[b].iterations);
+    const double* r = (it & 1) ? p.rbuf1 : p.rbuf0;
+    for (int k = threadIdx.x & 31; k < ng; k += 32) w.x[k] = p.slot_w[so + k] * __ldcg(r + p.slot_g[so + k]);
+    __syncwarp();
+    restrict_rows(p.P64 + p.off_P[s], m, ng, w, p.rcl + co);
+    __syncwarp();
+}
+
+__device__ void ph_final_pressure(const Params& p, int64_t s) {
+    if ((threadIdx.x & 31) != 0) return;
+    const int b = p.sub_inst[s];
+    const double* wcb = p.wc + p.inst_coff[b];
+    p.xp[s] = __ldcg(p.xp + s) + __ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]);
+}
+
+__device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
     const int ng = p.sub_ng[s], ni = p.sub_ni[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], cb = p.off_cell[s], ib = p.off_int[s];
-    for (int k = threadIdx.x; k < ng; k += kThreads) {
+    const int l = threadIdx.x & 31;
+    for (int k = l; k < ng; k += 32) {
         const int gi = p.slot_g[so + k];
         const double u = __ldcg(p.u0 + gi) + __ldcg(p.x + gi);
         if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.flux_out[p.g_fid[gi]] = u;
-        sm.xin[k] = u;
+        w.xin[k] = u;
     }
-    for (int r = threadIdx.x; r < nc; r += kThreads) sm.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
-    __syncthreads();
+    for (int r = l; r < nc; r += 32) w.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
+    __syncwarp();
     const double* G = p.Gpost + p.off_Gpost[s];
-    const int no = ni + nc;
+    const int no = ni + nc, nin = ng + nc;
     const double d = p.sub_d[s];
     const double xp = __ldcg(p.xp + s);
-    for (int o = threadIdx.x; o < no; o += kThreads) {
-        const double v = gemv_col<double, double>(G, no, ng + nc, sm.xin, o);
+    for (int o = l; o < no; o += 32) {
+        double a0 = 0.0, a1 = 0.0;
+        int j = 0;
+        for (; j + 1 < nin; j += 2) {
+            a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
+            a1 = fma(__ldg(G + (int64_t)(j + 1) * no + o), w.xin[j + 1], a1);
+        }
+        if (j < nin) a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
+        const double v = a0 + a1;
         if (o < ni) p.flux_out[p.int_fid[ib + o]] = v;
         else p.p_out[p.cell_gid[cb + o - ni]] = d * (xp + v);
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 // ---- the persistent solve kernel -------------------------------------------------------
-template <class T>
+template <class PR>
 __global__ void __launch_bounds__(kThreads) bddc_solve_kernel(Params p) {
     extern __shared__ double smem_base[];
-    Smem sm = carve(p, smem_base);
+    CtaSm sm = carve(p, smem_base);
+    WarpSm& w = sm.w;
     int64_t a, e;
     int staged;
-    my_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_step1<T>(p, s, sm);
+    warp_range(p.n_sub, a, e);
+    for (int64_t s = a; s < e; ++s) ph_step1<PR>(p, s, w);
     if (!grid_barrier(p.gsync)) return;
     staged = -1;
-    my_range(p.n_cunits, a, e);
-    for (int64_t u = a; u < e; ++u) ph_coarse(p, u, true, sm, staged);
+    cta_range(p.n_cunits, a, e);
+    for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
     if (!grid_barrier(p.gsync)) return;
-    my_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_u0<T>(p, s, sm);
+    warp_range(p.n_sub, a, e);
+    for (int64_t s = a; s < e; ++s) ph_u0<PR>(p, s, w);
     if (!grid_barrier(p.gsync)) return;
-    for (int64_t s = a; s < e; ++s) ph_step2(p, s, sm);
+    for (int64_t s = a; s < e; ++s) ph_step2<PR>(p, s, w);
     if (!grid_barrier(p.gsync)) return;
-    for (int64_t s = a; s < e; ++s) ph_fstar<T>(p, s, sm);
+    for (int64_t s = a; s < e; ++s) ph_fstar<PR>(p, s, w);
     if (!grid_barrier(p.gsync)) return;
     staged = -1;
-    my_range(p.n_cunits, a, e);
-    for (int64_t u = a; u < e; ++u) ph_coarse(p, u, false, sm, staged);
+    cta_range(p.n_cunits, a, e);
+    for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
     if (!grid_barrier(p.gsync)) return;
-    my_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_prolong<T>(p, s, sm);
+    warp_range(p.n_sub, a, e);
+    for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
     if (!grid_barrier(p.gsync)) return;
     for (int k = 0;; ++k) {
-        my_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_dirop(p, s, k, sm);
+        InstCache cache;
+        warp_range(p.n_sub, a, e);
+        for (int64_t s = a; s < e; ++s) ph_dirop<PR>(p, s, k, w, cache);
         if (!grid_barrier(p.gsync)) return;
         if (__ldcg(p.n_active) <= 0) break;
-        for (int64_t s = a; s < e; ++s) ph_update<T>(p, s, k, sm);
+        cache = InstCache();
+        for (int64_t s = a; s < e; ++s) ph_update<PR>(p, s, k, w, cache);
         if (!grid_barrier(p.gsync)) return;
         staged = -1;
-        my_range(p.n_cunits, a, e);
-        for (int64_t u = a; u < e; ++u) ph_coarse(p, u, false, sm, staged);
+        cta_range(p.n_cunits, a, e);
+        for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
         if (!grid_barrier(p.gsync)) return;
-        my_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_prolong<T>(p, s, sm);
+        warp_range(p.n_sub, a, e);
+        for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
         if (!grid_barrier(p.gsync)) return;
     }
-    my_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_post(p, s, sm);
+    if constexpr (PR::kMixed) {
+        // closing FP64 coarse pressure correction (every instance is done;
+        // the coarse phase runs in step-1 layout with a zero pressure part)
+        warp_range(p.n_sub, a, e);
+        for (int64_t s = a; s < e; ++s) ph_final_restrict(p, s, w);
+        if (!grid_barrier(p.gsync)) return;
+        cta_range(p.n_sub, a, e);
+        for (int64_t s = a; s < e; ++s) if (threadIdx.x == 0) p.prhs[s] = 0.0;
+        if (!grid_barrier(p.gsync)) return;
+        staged = -1;
+        cta_range(p.n_cunits, a, e);
+        for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
+        if (!grid_barrier(p.gsync)) return;
+        warp_range(p.n_sub, a, e);
+        for (int64_t s = a; s < e; ++s) ph_final_pressure(p, s);
+        if (!grid_barrier(p.gsync)) return;
+    }
+    warp_range(p.n_sub, a, e);
+    for (int64_t s = a; s < e; ++s) ph_post(p, s, w);
 }
 
 // ---- stand-alone operator / preconditioner kernels (grid-stride over units) --------
+template <class PR>
 __global__ void __launch_bounds__(kThreads) k_operator_local(Params p, const double* u, const double* p0) {
+    using S_t = typename PR::S_t;
     extern __shared__ double smem_base[];
-    Smem sm = carve(p, smem_base);
-    for (int64_t s = blockIdx.x; s < p.n_sub; s += gridDim.x) {
+    CtaSm sm = carve(p, smem_base);
+    WarpSm& w = sm.w;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < p.n_sub; s += W) {
         const int ng = p.sub_ng[s];
         const int64_t so = p.off_slot[s];
-        for (int k = threadIdx.x; k < ng; k += kThreads) sm.xs[k] = u[p.slot_g[so + k]];
-        __syncthreads();
-        const double* S = p.S + p.off_S[s];
+        for (int k = threadIdx.x & 31; k < ng; k += 32) w.x[k] = u[p.slot_g[so + k]];
+        __syncwarp();
+        const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
         const double pv = p0[s];
-        for (int k = threadIdx.x; k < ng; k += kThreads)
-            p.ql[so + k] = gemv_col<double, double>(S, ng, ng, sm.xs, k) + p.slot_dsig[so + k] * pv;
-        __syncthreads();
+        for (int k = threadIdx.x & 31; k < ng; k += 32)
+            p.ql[so + k] = gemv_out(S, ng, ng, w, k) + p.slot_dsig[so + k] * pv;
+        __syncwarp();
     }
 }
 
@@ -588,54 +848,65 @@ __global__ void k_assemble(int64_t n_slots, const double* loc, const int* slot_g
     }
 }
 
-template <class T>
+template <class PR>
 __global__ void __launch_bounds__(kThreads) k_precond_restrict(Params p, const double* r) {
     extern __shared__ double smem_base[];
-    Smem sm = carve(p, smem_base);
-    for (int64_t s = blockIdx.x; s < p.n_sub; s += gridDim.x) {
+    CtaSm sm = carve(p, smem_base);
+    WarpSm& w = sm.w;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < p.n_sub; s += W) {
         const int ng = p.sub_ng[s];
         const int64_t so = p.off_slot[s];
-        for (int k = threadIdx.x; k < ng; k += kThreads) {
+        for (int k = threadIdx.x & 31; k < ng; k += 32) {
             const double wr = p.slot_w[so + k] * r[p.slot_g[so + k]];
-            sm.xs[k] = wr;
+            w.x[k] = wr;
             p.rl[so + k] = wr;
         }
-        __syncthreads();
-        restrict_apply<T>(p, s, sm);
+        __syncwarp();
+        restrict_apply<PR>(p, s, w);
     }
 }
 
+template <class PR>
 __global__ void __launch_bounds__(kThreads) k_precond_coarse(Params p) {
     extern __shared__ double smem_base[];
-    Smem sm = carve(p, smem_base);
-    int staged = -1;
+    CtaSm sm = carve(p, smem_base);
     for (int64_t u = blockIdx.x; u < p.n_cunits; u += gridDim.x) {
-        staged = -1;
-        ph_coarse(p, u, false, sm, staged);
+        int staged = -1;
+        ph_coarse<PR>(p, u, false, sm.rhs, staged);
     }
 }
 
-template <class T>
+template <class PR>
 __global__ void __launch_bounds__(kThreads) k_precond_prolong(Params p, double* z0) {
+    using F_t = typename PR::F_t;
     extern __shared__ double smem_base[];
-    Smem sm = carve(p, smem_base);
-    for (int64_t s = blockIdx.x; s < p.n_sub; s += gridDim.x) {
+    CtaSm sm = carve(p, smem_base);
+    WarpSm& w = sm.w;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    for (int64_t s = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); s < p.n_sub; s += W) {
         const int b = p.sub_inst[s];
         const int ng = p.sub_ng[s], m = p.sub_m[s];
         const int64_t so = p.off_slot[s];
         const double* wcb = p.wc + p.inst_coff[b];
-        stage_wc(p, s, wcb, sm);
-        for (int k = threadIdx.x; k < ng; k += kThreads)
-            p.zl[so + k] = p.slot_w[so + k] * (prolong_one<T>(p, s, ng, m, sm.rhs, k) + p.yl[so + k]);
-        if (threadIdx.x == 0) z0[s] = wcb[p.inst_ncf[b] + p.sub_local[s]];
-        __syncthreads();
+        stage_wc(p, s, wcb, w);
+        const F_t* P = reinterpret_cast<const F_t*>(p.P) + p.off_P[s];
+        for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = prolong_out(P, m, ng, w, k);
+        __syncwarp();
+        if constexpr (PR::kMixed) {
+            face_sums(p, s, w.xin, w.tsum);
+            set_face_flux(p, s, w.xin, w.tsum, w.wcs);
+        }
+        for (int k = threadIdx.x & 31; k < ng; k += 32) p.zl[so + k] = p.slot_w[so + k] * (w.xin[k] + p.yl[so + k]);
+        if ((threadIdx.x & 31) == 0) z0[s] = wcb[p.inst_ncf[b] + p.sub_local[s]];
+        __syncwarp();
     }
 }
 
 // raw subassembled apply (no handle)
-__global__ void __launch_bounds__(kThreads) k_subassembled_local(int n_sub, const int* ng_arr, const int64_t* slot_off,
-                                                                 const int64_t* S_off, const double* S, const int* gidx,
-                                                                 const double* u, double* scratch) {
+__global__ void __launch_bounds__(128) k_subassembled_local(int n_sub, const int* ng_arr, const int64_t* slot_off,
+                                                            const int64_t* S_off, const double* S, const int* gidx,
+                                                            const double* u, double* scratch) {
     __shared__ double xs[1024];
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
         const int ng = ng_arr[s];
@@ -643,7 +914,11 @@ __global__ void __launch_bounds__(kThreads) k_subassembled_local(int n_sub, cons
         for (int k = threadIdx.x; k < ng; k += blockDim.x) xs[k] = u[gidx[so + k]];
         __syncthreads();
         const double* M = S + S_off[s];
-        for (int k = threadIdx.x; k < ng; k += blockDim.x) scratch[so + k] = gemv_col<double, double>(M, ng, ng, xs, k);
+        for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+            double acc = 0.0;
+            for (int j = 0; j < ng; ++j) acc = fma(__ldg(M + (int64_t)j * ng + k), xs[j], acc);
+            scratch[so + k] = acc;
+        }
         __syncthreads();
     }
 }
@@ -810,22 +1085,42 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     UP(slot_dsig, P.slot_dsig); UP(cslot_c, P.cslot_c); UP(cell_gid, P.cell_gid); UP(int_fid, P.int_fid);
     UP(g_fid, P.g_fid); UP(g_bsign, P.g_bsign); UP(c_slot_a, P.c_slot_a); UP(c_slot_b, P.c_slot_b);
     UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0);
-    UP(S, P.S); UP(Gpre, P.Gpre); UP(Gpost, P.Gpost); UP(Kinv, P.Kinv);
+    UP(Gpre, P.Gpre); UP(Gpost, P.Gpost); UP(P64, P.P64);
+    UP(slot_fcs, P.slot_fcs); UP(cslot_n, P.cslot_n); UP(slot_coef, P.slot_coef);
+    UP(slot_fperm, P.slot_fperm); UP(cslot_fstart, P.cslot_fstart);
     UP(inst_cfoff, h->inst_cfoff);
 #undef UP
     if (!rc) {
         if (opt.precision == BDDC_PREC_FP32) {
+            // the coarse inverse as FP32 pairs (hi, lo); F and Psi FP32; S FP64
+            auto pairs = [](const std::vector<double>& v) {
+                std::vector<float2> o(v.size());
+                for (size_t q = 0; q < v.size(); ++q) {
+                    const float hi = (float)v[q];
+                    o[q] = make_float2(hi, (float)(v[q] - (double)hi));
+                }
+                return o;
+            };
             const float *f = nullptr, *pp = nullptr;
+            const float2* k2 = nullptr;
+            const double* s64 = nullptr;
             rc = upload(h, P.F32, &f);
             if (!rc) rc = upload(h, P.P32, &pp);
+            if (!rc) rc = upload(h, P.S, &s64);
+            if (!rc) rc = upload(h, pairs(P.Kinv), &k2);
             p.F = f;
             p.P = pp;
+            p.S = s64;
+            p.Kinv = k2;
         } else {
-            const double *f = nullptr, *pp = nullptr;
+            const double *f = nullptr, *s64 = nullptr, *k64 = nullptr;
             rc = upload(h, P.F64, &f);
-            if (!rc) rc = upload(h, P.P64, &pp);
+            if (!rc) rc = upload(h, P.S, &s64);
+            if (!rc) rc = upload(h, P.Kinv, &k64);
             p.F = f;
-            p.P = pp;
+            p.P = p.P64;
+            p.S = s64;
+            p.Kinv = k64;
         }
     }
     const int64_t G = P.n_gamma, L = P.off_slot.back(), CL = P.off_cslot.back(), NS = P.n_sub;
@@ -851,13 +1146,15 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     p.max_ng = std::max(P.max_ng, 1);
     p.max_in_post = std::max(P.max_in_post, 1);
     p.max_ncn = std::max(P.max_ncn, 1);
-    h->smem = sizeof(double) * (size_t)(p.max_ng + p.max_in_post + p.max_ncn + 16) + sizeof(float) * (size_t)p.max_ng + 16;
+    p.max_m = std::max(P.max_m, 1);
+    h->smem = sizeof(double) * ((size_t)p.max_ncn +
+                                (size_t)kWarps * (2 * (size_t)p.max_ng + p.max_in_post + 2 * ((size_t)p.max_m + 1)));
     if (h->smem > 200 * 1024) {
         bddc_destroy(h);
         return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve
     }
-    const void* kfn = opt.precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<float>
-                                                      : (const void*)bddc_solve_kernel<double>;
+    const void* kfn = opt.precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<PrecMixed>
+                                                      : (const void*)bddc_solve_kernel<PrecFP64>;
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     int nb = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, h->smem);
@@ -880,6 +1177,7 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     }
     // algorithmic bytes (matrices once per use; vectors ~18 doubles per slot
     // and iteration)
+    // (the mixed path stores S and the coarse inverse as FP32 pairs: 8 bytes)
     const double fb = opt.precision == BDDC_PREC_FP32 ? 4.0 : 8.0;
     double it_b = 0.0, pre_b = 0.0, post_b = 0.0;
     for (int64_t s = 0; s < NS; ++s) {
@@ -941,8 +1239,8 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     cudaMemsetAsync(p.gsync, 0, sizeof(GridSync), st);
     cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);
     void* args[] = {&p};
-    const void* kfn = h->precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<float>
-                                                     : (const void*)bddc_solve_kernel<double>;
+    const void* kfn = h->precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<PrecMixed>
+                                                     : (const void*)bddc_solve_kernel<PrecFP64>;
     cudaEventRecord(h->ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(h->grid), dim3(kThreads), args, h->smem, st);
     cudaEventRecord(h->ev1, st);
@@ -999,6 +1297,41 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     return ret;
 }
 
+int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64_t* count) {
+    if (!h || !name) return BDDC_E_INVALID_ARG;
+    const Params& p = h->prm;
+    const std::string n(name);
+    const int64_t G = h->P.n_gamma, L = h->P.off_slot.back(), CL = h->P.off_cslot.back(), NS = h->P.n_sub;
+    const double* src = nullptr;
+    int64_t len = 0;
+    if (n == "x") { src = p.x; len = G; }
+    else if (n == "r0") { src = p.rbuf0; len = G; }
+    else if (n == "r1") { src = p.rbuf1; len = G; }
+    else if (n == "d0") { src = p.dbuf0; len = G; }
+    else if (n == "d1") { src = p.dbuf1; len = G; }
+    else if (n == "g") { src = p.g; len = G; }
+    else if (n == "u0") { src = p.u0; len = G; }
+    else if (n == "ql") { src = p.ql; len = L; }
+    else if (n == "zl") { src = p.zl; len = L; }
+    else if (n == "yl") { src = p.yl; len = L; }
+    else if (n == "rl") { src = p.rl; len = L; }
+    else if (n == "tl") { src = p.tl; len = L; }
+    else if (n == "rcl") { src = p.rcl; len = CL; }
+    else if (n == "wc") { src = p.wc; len = h->P.n_coarse_vec; }
+    else if (n == "xp") { src = p.xp; len = NS; }
+    else if (n == "zp") { src = p.zp; len = NS; }
+    else if (n == "prhs") { src = p.prhs; len = NS; }
+    else if (n == "part_rr") { src = p.part_rr; len = NS; }
+    else if (n == "part_rz") { src = p.part_rz; len = NS; }
+    else if (n == "part_dq") { src = p.part_dq; len = NS; }
+    else return BDDC_E_INVALID_ARG;
+    if (count) *count = len;
+    if (dst && len) {
+        if (cudaMemcpy(dst, src, len * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
+    }
+    return BDDC_OK;
+}
+
 int bddc_get_stats(const bddc_handle* h, int instance, bddc_stats* out) {
     if (!h || !out || instance < 0 || instance >= h->n_inst) return BDDC_E_INVALID_ARG;
     *out = h->stats[instance];
@@ -1017,8 +1350,9 @@ int bddc_apply_operator(bddc_handle* h, const double* u, const double* p0, doubl
     if (!is_device_ptr(u) || !is_device_ptr(p0) || !is_device_ptr(q))
         return set_err(h, BDDC_E_INVALID_ARG, "device pointers required");
     Params p = h->prm;
-    const int grid = (int)std::min<int64_t>(p.n_sub, 4096);
-    k_operator_local<<<grid, kThreads, h->smem, h->stream>>>(p, u, p0);
+    const int grid = (int)std::min<int64_t>((p.n_sub + kWarps - 1) / kWarps, 4096);
+    if (h->precision == BDDC_PREC_FP32) k_operator_local<PrecMixed><<<grid, kThreads, h->smem, h->stream>>>(p, u, p0);
+    else k_operator_local<PrecFP64><<<grid, kThreads, h->smem, h->stream>>>(p, u, p0);
     const int64_t L = h->P.off_slot.back();
     k_assemble<<<(int)std::min<int64_t>((L + 255) / 256, 4096), 256, 0, h->stream>>>(L, p.ql, p.slot_g, p.slot_partner, q);
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -1031,17 +1365,16 @@ int bddc_apply_preconditioner(bddc_handle* h, const double* r, double* z, double
         return set_err(h, BDDC_E_INVALID_ARG, "device pointers required");
     Params p = h->prm;
     cudaMemsetAsync(p.st, 0, sizeof(InstState) * h->n_inst, h->stream);
-    const int grid = (int)std::min<int64_t>(p.n_sub, 4096);
+    const int grid = (int)std::min<int64_t>((p.n_sub + kWarps - 1) / kWarps, 4096);
+    const int cgrid = (int)std::min<int64_t>(p.n_cunits, 4096);
     if (h->precision == BDDC_PREC_FP32) {
-        k_precond_restrict<float><<<grid, kThreads, h->smem, h->stream>>>(p, r);
+        k_precond_restrict<PrecMixed><<<grid, kThreads, h->smem, h->stream>>>(p, r);
+        k_precond_coarse<PrecMixed><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        k_precond_prolong<PrecMixed><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
     } else {
-        k_precond_restrict<double><<<grid, kThreads, h->smem, h->stream>>>(p, r);
-    }
-    k_precond_coarse<<<(int)std::min<int64_t>(p.n_cunits, 4096), kThreads, h->smem, h->stream>>>(p);
-    if (h->precision == BDDC_PREC_FP32) {
-        k_precond_prolong<float><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
-    } else {
-        k_precond_prolong<double><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
+        k_precond_restrict<PrecFP64><<<grid, kThreads, h->smem, h->stream>>>(p, r);
+        k_precond_coarse<PrecFP64><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        k_precond_prolong<PrecFP64><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
     }
     const int64_t L = h->P.off_slot.back();
     k_assemble<<<(int)std::min<int64_t>((L + 255) / 256, 4096), 256, 0, h->stream>>>(L, p.zl, p.slot_g, p.slot_partner, z);
@@ -1063,8 +1396,8 @@ int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset
     if (cudaMemcpy(hng.data(), ng, sizeof(int) * n_sub, cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
     for (int v : hng)
         if (v < 0 || v > 1024) return BDDC_E_INVALID_ARG;
-    k_subassembled_local<<<std::min(n_sub, 4096), kThreads, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u,
-                                                                     slot_scratch);
+    k_subassembled_local<<<std::min(n_sub, 4096), 128, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u,
+                                                                slot_scratch);
     k_assemble<<<(int)std::min<int64_t>((n_slots + 255) / 256, 4096), 256, 0, st>>>(n_slots, slot_scratch, gidx, partner, q);
     return cudaGetLastError() == cudaSuccess ? BDDC_OK : BDDC_E_CUDA;
 }

@@ -1,17 +1,26 @@
-// Device-side data layout and phase functions of the BDDC solve.
+// Device-side data layout of the BDDC solve.
 //
 // One persistent cooperative kernel runs Algorithm 1 of the paper for every
 // instance of a batch: Step 1 (coarse solve), Step 2 (subdomain solves),
 // Step 3 (CG on the interface with the BDDC preconditioner of Algorithm 2)
-// and the post-correction.  Phases are separated by a grid barrier; work
-// units are subdomains (or blocks of coarse rows) assigned to CTAs in
-// contiguous chunks.
+// and the post-correction.  Phases are separated by a grid barrier.  Per
+// subdomain work units are processed by one warp each (global warps take
+// contiguous chunks of units); coarse work units are blocks of coarse rows
+// processed by one CTA each.
 //
 // Conventions of the packed data are those of bddc_internal.hpp: every
 // per-subdomain operator is stored input-major (entry (out, in) at
-// [in * n_out + out]) so that the thread computing one output reads
+// [in * n_out + out]) so that the lane computing one output reads
 // consecutive addresses together with its neighbours; the restriction
 // Psi^T r is a warp dot product over a contiguous row of PsiT.
+//
+// Two precisions: FP64 everywhere (S, F, Psi, coarse inverse), or the mixed
+// path where the preconditioner is cheaper: F and Psi in FP32 and the coarse
+// inverse stored as FP32 pairs (hi + lo, 48 significant bits) applied with
+// compensated FP32 arithmetic (FP64 arithmetic on GB300 runs at about 1/64
+// of the FP32 rate).  The operator S stays FP64 in both paths.  The mixed
+// path keeps the preconditioner output exactly balanced (a per-face net-flux
+// correction) and ends with an FP64 coarse pressure correction.
 #pragma once
 
 #include <cstdint>
@@ -19,8 +28,9 @@
 
 namespace bddc {
 
-constexpr int kThreads = 128;
-constexpr int kCoarseRows = 8;              // coarse rows per work unit
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCoarseRows = 16;             // coarse rows per work unit
 constexpr long long kSpinLimit = 1LL << 24; // grid-barrier spins before giving up
 
 struct GridSync {
@@ -30,7 +40,7 @@ struct GridSync {
     int pad;
 };
 
-// per-instance CG state (written by the instance's owner CTA)
+// per-instance CG state (written by the warp that owns the instance)
 struct InstState {
     int done;        // 1 once the instance left the CG loop
     int status;      // BDDC_OK / BDDC_E_NOT_CONVERGED / BDDC_E_BREAKDOWN
@@ -53,15 +63,19 @@ struct Params {
     const int *slot_g, *slot_partner;
     const double *slot_w, *slot_dsig;
     const int* cslot_c;
+    const int *slot_fcs, *cslot_n;   // net-flux row of each slot; dofs per net-flux row
+    const double* slot_coef;
+    const int *slot_fperm, *cslot_fstart;  // slots grouped by net-flux row
     const int64_t *cell_gid, *int_fid, *g_fid;
     const double* g_bsign;
     const int *c_slot_a, *c_slot_b;
     // coarse units
     int64_t n_cunits;
     const int *cunit_inst, *cunit_row0;
-    // matrices
-    const double *S, *Gpre, *Gpost, *Kinv;
-    const void *F, *P;
+    // matrices: S is double; Kinv is double (FP64 path) or float2 pairs
+    // (mixed); F and P are double or float; P64 is always FP64
+    const void *S, *F, *P, *Kinv;
+    const double *P64, *Gpre, *Gpost;
     // work vectors
     double *x, *rbuf0, *rbuf1, *dbuf0, *dbuf1, *g, *u0;        // interface
     double *ql, *zl, *yl, *rl, *tl;                            // local slots
@@ -79,7 +93,7 @@ struct Params {
     // control
     int maxit;
     double tol;
-    int max_ng, max_in_post, max_ncn;
+    int max_ng, max_in_post, max_ncn, max_m;
 };
 
 }  // namespace bddc

@@ -98,6 +98,9 @@ struct Sub {
     std::vector<double> S, GpreT, GpostT, Lchol;
     std::vector<double> C, F, PsiT;
     std::vector<int> cid;
+    std::vector<int> fcs;        // interface slot -> local row of its net-flux constraint
+    std::vector<double> fcoef;   // coefficient of that row on the slot
+    std::vector<int> rown;       // local row -> face dofs (net-flux rows), 0 otherwise
 };
 
 struct Face {
@@ -461,53 +464,96 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
     std::vector<int> piv;
     if (!lu(nq, Qm.data(), piv)) return {BDDC_E_SETUP, "singular local pressure Schur complement"};
 
-    // solve for the ng + nc input columns
+    // solve for the ng + nc input columns, with two steps of iterative
+    // refinement against the exact sparse local operator (the elimination
+    // loses accuracy in proportion to the permeability contrast)
     const int ncol = ng + nc;
-    std::vector<double> T((size_t)ncol * ni, 0.0);       // t = A_II^{-1} x_u per column
-    std::vector<double> Xp((size_t)nq * ncol, 0.0);      // pressure rhs, nq x ncol
+    std::vector<double> XU((size_t)ncol * ni, 0.0);    // interior rhs per column
+    std::vector<double> XP((size_t)nq * ncol, 0.0);    // pressure/mu rhs, nq x ncol
     for (int j = 0; j < ng; ++j) {
         const int r = gcell[j], a = gaxis[j];
-        const double s = S.cs[(size_t)r * dim + a];
+        const double sc = S.cs[(size_t)r * dim + a];
         // x_u = -A_IG e_j: the other face of the cell along the same axis
         const int other = gside[j] == 0 ? S.chi[(size_t)r * dim + a] : S.clo[(size_t)r * dim + a];
-        if (other >= ng) T[(size_t)j * ni + (other - ng)] = -kMassOff * s;
+        if (other >= ng) XU[(size_t)j * ni + (other - ng)] = -kMassOff * sc;
         // x_p = -dB_G e_j
-        Xp[(size_t)r * ncol + j] = -d * (gside[j] == 0 ? 1.0 : -1.0);
+        XP[(size_t)r * ncol + j] = -d * (gside[j] == 0 ? 1.0 : -1.0);
     }
-    for (int r = 0; r < nc; ++r) Xp[(size_t)r * ncol + ng + r] = -d * vol;  // d <f, q_c> per unit f
-    for (int j = 0; j < ncol; ++j) {
-        double* t = &T[(size_t)j * ni];
-        chain_solve(ch, t);
-        dBI(t, col.data());
-        for (int r = 0; r < nc; ++r) Xp[(size_t)r * ncol + j] -= col[r];
+    for (int r = 0; r < nc; ++r) XP[(size_t)r * ncol + ng + r] = -d * vol;  // d <f, q_c> per unit f
+    // solve K_I [yu; yp; ymu] = [xu; xp; xmu] for all columns
+    auto solve_all = [&](const std::vector<double>& xu, const std::vector<double>& xp,
+                         std::vector<double>& yu, std::vector<double>& ypm) {
+        yu = xu;
+        ypm = xp;
+        for (int j = 0; j < ncol; ++j) {
+            double* t = &yu[(size_t)j * ni];
+            chain_solve(ch, t);
+            dBI(t, col.data());
+            for (int r = 0; r < nc; ++r) ypm[(size_t)r * ncol + j] -= col[r];
+        }
+        lu_solve(nq, Qm.data(), piv, ypm.data(), ncol);
+        for (int j = 0; j < ncol; ++j) {
+            double* t = &yu[(size_t)j * ni];
+            for (int r = 0; r < nc; ++r) {
+                const double yp = ypm[(size_t)r * ncol + j];
+                if (yp == 0.0) continue;
+                const double* y = &Y[(size_t)r * ni];
+                for (int e = 0; e < ni; ++e) t[e] -= y[e] * yp;
+            }
+        }
+    };
+    std::vector<double> YU, YPM;
+    solve_all(XU, XP, YU, YPM);
+    {
+        std::vector<double> RU((size_t)ncol * ni), RP((size_t)nq * ncol), DU, DPM;
+        for (int pass = 0; pass < 2; ++pass) {
+            // residual of K_I y against the right-hand side
+            for (int j = 0; j < ncol; ++j) {
+                const double* yu = &YU[(size_t)j * ni];
+                double* ru = &RU[(size_t)j * ni];
+                for (int e = 0; e < ni; ++e) ru[e] = XU[(size_t)j * ni + e];
+                double ymu = YPM[(size_t)nc * ncol + j], sump = 0.0;
+                for (int r = 0; r < nc; ++r) {
+                    const double yp = YPM[(size_t)r * ncol + j];
+                    sump += yp;
+                    double divr = 0.0;
+                    for (int a = 0; a < dim; ++a) {
+                        const double sc = S.cs[(size_t)r * dim + a];
+                        const int l = S.clo[(size_t)r * dim + a], h = S.chi[(size_t)r * dim + a];
+                        const bool li = l >= ng, hi = h >= ng;
+                        const double vl = li ? yu[l - ng] : 0.0, vh = hi ? yu[h - ng] : 0.0;
+                        if (li) ru[l - ng] -= kMassDiag * sc * vl + kMassOff * sc * vh + d * yp;
+                        if (hi) ru[h - ng] -= kMassOff * sc * vl + kMassDiag * sc * vh - d * yp;
+                        divr += d * (vl - vh);
+                    }
+                    RP[(size_t)r * ncol + j] = XP[(size_t)r * ncol + j] - divr - vol * ymu;
+                }
+                RP[(size_t)nc * ncol + j] = XP[(size_t)nc * ncol + j] - vol * sump;
+            }
+            solve_all(RU, RP, DU, DPM);
+            for (size_t q = 0; q < YU.size(); ++q) YU[q] += DU[q];
+            for (size_t q = 0; q < YPM.size(); ++q) YPM[q] += DPM[q];
+        }
     }
-    lu_solve(nq, Qm.data(), piv, Xp.data(), ncol);
-    // y_u = t - Y y_p ; outputs per column
+    // outputs per column
     S.GpostT.assign((size_t)ncol * (ni + nc), 0.0);
     S.S.assign((size_t)ng * ng, 0.0);
     S.GpreT.assign((size_t)nc * ng, 0.0);
-    std::vector<double> yu(ni);
     for (int j = 0; j < ncol; ++j) {
-        for (int e = 0; e < ni; ++e) yu[e] = T[(size_t)j * ni + e];
-        for (int r = 0; r < nc; ++r) {
-            const double yp = Xp[(size_t)r * ncol + j];
-            if (yp == 0.0) continue;
-            const double* y = &Y[(size_t)r * ni];
-            for (int e = 0; e < ni; ++e) yu[e] -= y[e] * yp;
-        }
+        const double* yu = &YU[(size_t)j * ni];
         double* post = &S.GpostT[(size_t)j * (ni + nc)];
         for (int e = 0; e < ni; ++e) post[e] = yu[e];
-        for (int r = 0; r < nc; ++r) post[ni + r] = Xp[(size_t)r * ncol + j];
+        for (int r = 0; r < nc; ++r) post[ni + r] = YPM[(size_t)r * ncol + j];
         // interface residual r_G = A_GI y_u + A_GG u_G + dB_G^T y_p
         for (int k = 0; k < ng; ++k) {
             const int r = gcell[k], a = gaxis[k];
-            const double s = S.cs[(size_t)r * dim + a];
+            const double sc = S.cs[(size_t)r * dim + a];
             const int other = gside[k] == 0 ? S.chi[(size_t)r * dim + a] : S.clo[(size_t)r * dim + a];
-            double v = d * (gside[k] == 0 ? 1.0 : -1.0) * Xp[(size_t)r * ncol + j];
-            if (other >= ng) v += kMassOff * s * yu[other - ng];
+            double v = d * (gside[k] == 0 ? 1.0 : -1.0) * YPM[(size_t)r * ncol + j];
+            if (other >= ng) v += kMassOff * sc * yu[other - ng];
             if (j < ng) {
-                if (k == j) v += kMassDiag * s;
-                if (other >= 0 && other < ng && other == j) v += kMassOff * s;
+                if (k == j) v += kMassDiag * sc;
+                if (other >= 0 && other < ng && other == j) v += kMassOff * sc;
             }
             if (j < ng) S.S[(size_t)j * ng + k] = v;
             else S.GpreT[(size_t)(j - ng) * ng + k] = v;
@@ -558,7 +604,10 @@ SetupResult correction_maps(Sub& S) {
             const double v = 0.5 * (S.F[(size_t)a * ng + b] + S.F[(size_t)b * ng + a]);
             S.F[(size_t)a * ng + b] = S.F[(size_t)b * ng + a] = v;
         }
-    // Psi = (I - F S) C^T (C C^T)^{-1}
+    // Psi solves [S C^T; C 0] [Psi; Lam] = [0; I]: Psi = C^+ R2 + Z eta with
+    // (Z^T S Z) eta = Z^T (R1 - S C^+ R2), then two steps of iterative
+    // refinement against S (the null-space solve loses accuracy in
+    // proportion to the conditioning of S)
     std::vector<double> CCt((size_t)m * m, 0.0);
     for (int a = 0; a < m; ++a)
         for (int b = 0; b < m; ++b) {
@@ -567,35 +616,77 @@ SetupResult correction_maps(Sub& S) {
             CCt[(size_t)a * m + b] = v;
         }
     if (m > 0 && !chol(m, CCt.data())) return {BDDC_E_SETUP, "dependent constraint rows"};
-    std::vector<double> Cp((size_t)ng * m);    // C^T (C C^T)^{-1}, ng x m
-    {
-        std::vector<double> Ct((size_t)m * ng);  // (C C^T)^{-1} C, m x ng
-        for (size_t q = 0; q < Ct.size(); ++q) Ct[q] = S.C[q];
-        chol_solve(m, CCt.data(), Ct.data(), ng);
+    // constrained solve for m right-hand-side columns: R1 (ng x m), R2 (m x m)
+    auto csolve = [&](const std::vector<double>& R1, const std::vector<double>& R2, std::vector<double>& X) {
+        // y = C^+ R2 = C^T (C C^T)^{-1} R2
+        std::vector<double> T(R2);
+        if (m > 0) chol_solve(m, CCt.data(), T.data(), m);
+        std::vector<double> y((size_t)ng * m, 0.0);
         for (int i = 0; i < ng; ++i)
-            for (int a = 0; a < m; ++a) Cp[(size_t)i * m + a] = Ct[(size_t)a * ng + i];
+            for (int a = 0; a < m; ++a) {
+                const double c = S.C[(size_t)a * ng + i];
+                if (c == 0.0) continue;
+                for (int b = 0; b < m; ++b) y[(size_t)i * m + b] += c * T[(size_t)a * m + b];
+            }
+        // g = R1 - S y ; eta = (Z^T S Z)^{-1} Z^T g
+        std::vector<double> g(R1);
+        for (int i = 0; i < ng; ++i)
+            for (int k = 0; k < ng; ++k) {
+                const double sv = S.S[(size_t)i * ng + k];
+                if (sv == 0.0) continue;
+                for (int b = 0; b < m; ++b) g[(size_t)i * m + b] -= sv * y[(size_t)k * m + b];
+            }
+        std::vector<double> eta((size_t)nz * m, 0.0);
+        for (int c = 0; c < nz; ++c)
+            for (int i = 0; i < ng; ++i) {
+                const double z = Z[(size_t)i * nz + c];
+                if (z == 0.0) continue;
+                for (int b = 0; b < m; ++b) eta[(size_t)c * m + b] += z * g[(size_t)i * m + b];
+            }
+        if (nz > 0) chol_solve(nz, ZSZ.data(), eta.data(), m);
+        X = y;
+        for (int i = 0; i < ng; ++i)
+            for (int c = 0; c < nz; ++c) {
+                const double z = Z[(size_t)i * nz + c];
+                if (z == 0.0) continue;
+                for (int b = 0; b < m; ++b) X[(size_t)i * m + b] += z * eta[(size_t)c * m + b];
+            }
+    };
+    std::vector<double> R1((size_t)ng * m, 0.0), R2((size_t)m * m, 0.0), Psi, dX;
+    for (int a = 0; a < m; ++a) R2[(size_t)a * m + a] = 1.0;
+    csolve(R1, R2, Psi);
+    for (int pass = 0; pass < 2; ++pass) {
+        // residuals: R2 = I - C Psi ; R1 = -S Psi projected off the row space of C
+        // (the multiplier absorbs the row-space part)
+        std::vector<double> SP((size_t)ng * m, 0.0);
+        for (int i = 0; i < ng; ++i)
+            for (int k = 0; k < ng; ++k) {
+                const double sv = S.S[(size_t)i * ng + k];
+                if (sv == 0.0) continue;
+                for (int b = 0; b < m; ++b) SP[(size_t)i * m + b] += sv * Psi[(size_t)k * m + b];
+            }
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) {
+                double v = (a == b) ? 1.0 : 0.0;
+                for (int i = 0; i < ng; ++i) v -= S.C[(size_t)a * ng + i] * Psi[(size_t)i * m + b];
+                R2[(size_t)a * m + b] = v;
+            }
+        for (size_t q = 0; q < SP.size(); ++q) R1[q] = -SP[q];
+        csolve(R1, R2, dX);
+        for (size_t q = 0; q < Psi.size(); ++q) Psi[q] += dX[q];
     }
-    std::vector<double> SCp((size_t)ng * m, 0.0), FSCp((size_t)ng * m, 0.0);
-    for (int i = 0; i < ng; ++i)
-        for (int k = 0; k < ng; ++k) {
-            const double s = S.S[(size_t)i * ng + k];
-            if (s == 0.0) continue;
-            for (int a = 0; a < m; ++a) SCp[(size_t)i * m + a] += s * Cp[(size_t)k * m + a];
-        }
-    for (int i = 0; i < ng; ++i)
-        for (int k = 0; k < ng; ++k) {
-            const double f = S.F[(size_t)i * ng + k];
-            if (f == 0.0) continue;
-            for (int a = 0; a < m; ++a) FSCp[(size_t)i * m + a] += f * SCp[(size_t)k * m + a];
-        }
     S.PsiT.assign((size_t)m * ng, 0.0);
     for (int i = 0; i < ng; ++i)
-        for (int a = 0; a < m; ++a) S.PsiT[(size_t)a * ng + i] = Cp[(size_t)i * m + a] - FSCp[(size_t)i * m + a];
+        for (int a = 0; a < m; ++a) S.PsiT[(size_t)a * ng + i] = Psi[(size_t)i * m + a];
     return {};
 }
 
 void gather_constraints(Inst& I) {
-    for (Sub& S : I.subs) { S.C.clear(); S.cid.clear(); S.m = 0; }
+    for (Sub& S : I.subs) {
+        S.C.clear(); S.cid.clear(); S.m = 0; S.rown.clear();
+        S.fcs.assign(S.ng, -1);
+        S.fcoef.assign(S.ng, 0.0);
+    }
     for (const Face& F : I.faces) {
         for (int side = 0; side < (F.dir ? 1 : 2); ++side) {
             Sub& S = I.subs[side == 0 ? F.i : F.j];
@@ -606,6 +697,12 @@ void gather_constraints(Inst& I) {
             for (size_t rw = 0; rw < F.rows.size(); ++rw) {
                 std::vector<double> row(S.ng, 0.0);
                 for (size_t q = 0; q < pos.size(); ++q) row[pos[q]] = F.rows[rw][q];
+                if (rw == 0)  // the face's net-flux row (Assumption 1)
+                    for (size_t q = 0; q < pos.size(); ++q) {
+                        S.fcs[pos[q]] = S.m;
+                        S.fcoef[pos[q]] = F.rows[0][q];
+                    }
+                S.rown.push_back(rw == 0 ? (int)pos.size() : 0);
                 S.C.insert(S.C.end(), row.begin(), row.end());
                 S.cid.push_back(F.cids[rw]);
                 S.m++;
@@ -951,12 +1048,12 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             P.off_Gpre.push_back(oGpre); P.off_Gpost.push_back(oGpost);
             P.S.insert(P.S.end(), S.S.begin(), S.S.end());
             oS += (int64_t)S.ng * S.ng;
+            P.P64.insert(P.P64.end(), S.PsiT.begin(), S.PsiT.end());
             if (opt.precision == BDDC_PREC_FP32) {
                 for (double v : S.F) P.F32.push_back((float)v);
                 for (double v : S.PsiT) P.P32.push_back((float)v);
             } else {
                 P.F64.insert(P.F64.end(), S.F.begin(), S.F.end());
-                P.P64.insert(P.P64.end(), S.PsiT.begin(), S.PsiT.end());
             }
             oF += (int64_t)S.ng * S.ng;
             oP += (int64_t)S.m * S.ng;
@@ -969,10 +1066,22 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                 P.slot_g.push_back((int)(goff + g));
                 P.slot_w.push_back(S.w[k]);
                 P.slot_dsig.push_back(S.d * S.sigma[k]);
+                P.slot_fcs.push_back(S.fcs[k]);
+                P.slot_coef.push_back(S.fcoef[k]);
                 if (sa[g] < 0) sa[g] = (int)(slot + k); else sb[g] = (int)(slot + k);
+            }
+            {
+                int start = 0;
+                for (int a = 0; a < S.m; ++a) {
+                    if (S.rown[a] == 0) { P.cslot_fstart.push_back(-1); continue; }
+                    P.cslot_fstart.push_back(start);
+                    for (int k = 0; k < S.ng; ++k)
+                        if (S.fcs[k] == a) { P.slot_fperm.push_back(k); ++start; }
+                }
             }
             for (int a = 0; a < S.m; ++a) {
                 P.cslot_c.push_back(S.cid[a]);
+                P.cslot_n.push_back(S.rown[a]);
                 const int c = S.cid[a];
                 if (ca[c] < 0) ca[c] = (int)(cslot + a); else cb[c] = (int)(cslot + a);
             }
@@ -1020,15 +1129,15 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
     const std::string n(name ? name : "");
 #define E(x) if (n == #x) return export_vec(P.x, dst, count, eb)
     E(sub_inst); E(sub_ng); E(sub_ni); E(sub_nc); E(sub_m); E(sub_local); E(slot_g); E(slot_partner);
-    E(cslot_c); E(c_slot_a); E(c_slot_b); E(g_slot_a); E(g_slot_b);
+    E(cslot_c); E(c_slot_a); E(c_slot_b); E(g_slot_a); E(g_slot_b); E(slot_fcs); E(cslot_n); E(slot_coef); E(slot_fperm); E(cslot_fstart);
     E(inst_goff); E(inst_ng); E(inst_coff); E(inst_ncn); E(inst_ncf); E(inst_kinv_off); E(inst_s0); E(inst_s1);
     E(inst_face_off); E(inst_nfaces); E(inst_cell_off); E(inst_ncells); E(off_S); E(off_F); E(off_P);
     E(off_Gpre); E(off_Gpost); E(off_slot); E(off_cslot); E(off_cell); E(off_int); E(cell_gid); E(int_fid); E(g_fid);
-    E(inst_vol); E(inst_omega); E(sub_d); E(slot_w); E(slot_dsig); E(g_bsign); E(S); E(Gpre); E(Gpost); E(Kinv);
+    E(inst_vol); E(inst_omega); E(sub_d); E(slot_w); E(slot_dsig); E(g_bsign); E(S); E(Gpre); E(Gpost); E(Kinv); E(P64);
 #undef E
     if (n == "F" || n == "P") {
         const bool isF = n == "F";
-        const std::vector<double>& v64 = isF ? P.F64 : P.P64;
+        const std::vector<double>& v64 = isF ? P.F64 : (P.P32.empty() ? P.P64 : std::vector<double>());
         const std::vector<float>& v32 = isF ? P.F32 : P.P32;
         if (!v64.empty()) return export_vec(v64, dst, count, eb);
         if (count) *count = (int64_t)v32.size();

@@ -20,3 +20,13 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "slow" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_sessionstart(session):
+    """Build the in-tree library if it is missing or stale (nvcc is on both
+    the build host and the GPU machine)."""
+    try:
+        from paper_1901_02090_gb300.build import build
+        build()
+    except Exception as exc:  # the import of the binding will report it
+        sys.stderr.write(f"[conftest] building libbddc.so failed: {exc}\n")

@@ -21,7 +21,7 @@ class Packed:
                      "inst_cell_off", "inst_ncells", "off_S", "off_F", "off_P", "off_Gpre", "off_Gpost",
                      "off_slot", "off_cslot", "off_cell", "off_int", "cell_gid", "int_fid", "g_fid",
                      "inst_vol", "sub_d", "slot_w", "slot_dsig", "g_bsign", "S", "F", "P", "Gpre",
-                     "Gpost", "Kinv"):
+                     "Gpost", "Kinv", "slot_fcs", "cslot_n", "slot_coef", "P64"):
             setattr(self, name, hs.get(name))
         self.n_sub = len(self.sub_ng)
         self.n_inst = len(self.inst_ng)
@@ -37,8 +37,13 @@ class Packed:
         return np.arange(a, b)
 
 
-def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
-    """Returns (flux, pressure, iterations per instance, alphas, betas)."""
+def emulate_solve(P: Packed, f, bc, tol, maxit=5000, mixed=False):
+    """Returns (flux, pressure, iterations per instance, alphas, betas).
+
+    mixed=True replays the mixed-precision kernel: F and Psi applied as
+    P_Z F P_Z and Psi_0 + P_Z Psi (P_Z removes each face's net flux, Psi_0
+    carries the exact unit net fluxes), and the closing FP64 coarse pressure
+    correction (F and P must then hold the FP32-rounded operators)."""
     G, ns = P.G, P.n_sub
     ng, m, nc, ni = P.sub_ng, P.sub_m, P.sub_nc, P.sub_ni
     S = [P.mat(P.S, P.off_S, s, ng[s], ng[s]) for s in range(ns)]
@@ -53,6 +58,51 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
     cells = [P.cell_gid[P.off_cell[s]:P.off_cell[s + 1]] for s in range(ns)]
     ints = [P.int_fid[P.off_int[s]:P.off_int[s + 1]] for s in range(ns)]
     inst = P.sub_inst
+    fcs = [P.slot_fcs[sl] for sl in slots]
+    coef = [P.slot_coef[sl] for sl in slots]
+    cnt = [P.cslot_n[P.off_cslot[s]:P.off_cslot[s + 1]] for s in range(ns)]
+
+    def pz(s, v):
+        """Remove each face's net flux (symmetric projection P_Z)."""
+        v = v.copy()
+        for a in range(m[s]):
+            if cnt[s][a] == 0:
+                continue
+            sel = fcs[s] == a
+            v[sel] -= coef[s][sel] * np.sum(coef[s][sel] * v[sel]) / cnt[s][a]
+        return v
+
+    def psi0t(s, r):
+        """Psi_0^T r: the exact unit-net-flux part of the coarse basis."""
+        out = np.zeros(m[s])
+        for a in range(m[s]):
+            if cnt[s][a]:
+                sel = fcs[s] == a
+                out[a] = np.sum(coef[s][sel] * r[sel]) / cnt[s][a]
+        return out
+
+    def psi0(s, wcs):
+        out = np.zeros(ng[s])
+        for a in range(m[s]):
+            if cnt[s][a]:
+                sel = fcs[s] == a
+                out[sel] += coef[s][sel] * wcs[a] / cnt[s][a]
+        return out
+
+    def prolong(s, wcs):
+        if not mixed:
+            return PsiT[s].T @ wcs
+        return psi0(s, wcs) + pz(s, PsiT[s].T @ wcs)
+
+    def restrict(s, r):
+        if not mixed:
+            return PsiT[s] @ r
+        return psi0t(s, r) + PsiT[s] @ pz(s, r)
+
+    def fapply(s, r):
+        if not mixed:
+            return F[s] @ r
+        return pz(s, F[s] @ pz(s, r))
 
     def assemble(parts):
         out = np.zeros(G)
@@ -78,7 +128,7 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
     rc = [PsiT[s] @ (w[s] * g[gl[s]]) for s in range(ns)]
     prhs = np.array([P.sub_d[s] * P.inst_vol[inst[s]] * np.sum(-f[cells[s]]) for s in range(ns)])
     wc = coarse(rc, prhs)
-    u0 = assemble([w[s] * (PsiT[s].T @ wc[inst[s]][cid[s]]) for s in range(ns)])
+    u0 = assemble([w[s] * prolong(s, wc[inst[s]][cid[s]]) for s in range(ns)])
     # Step 2 and f*
     fstar = g - assemble([S[s] @ u0[gl[s]] + Gpre[s] @ f[cells[s]] for s in range(ns)])
     scale = np.zeros(P.n_inst)
@@ -88,8 +138,8 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
 
     def precond(r):
         rl = [w[s] * r[gl[s]] for s in range(ns)]
-        wc = coarse([PsiT[s] @ rl[s] for s in range(ns)])
-        zl = [PsiT[s].T @ wc[inst[s]][cid[s]] + F[s] @ rl[s] for s in range(ns)]
+        wc = coarse([restrict(s, rl[s]) for s in range(ns)])
+        zl = [prolong(s, wc[inst[s]][cid[s]]) + fapply(s, rl[s]) for s in range(ns)]
         z = assemble([w[s] * zl[s] for s in range(ns)])
         zp = np.array([wc[inst[s]][P.inst_ncf[inst[s]] + P.sub_local[s]] for s in range(ns)])
         return z, zp
@@ -112,9 +162,10 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
     rho0 = rho.copy()
     r0 = np.array([np.linalg.norm(r[islc[b]]) for b in range(P.n_inst)])
     for b in range(P.n_inst):
-        if r0[b] <= 1e-14 * scale[b]:
+        if r0[b] <= 1e-14 * scale[b] or rho[b] <= 0.0:
             done[b] = True
-            xp[sslc[b]] += zp[sslc[b]]
+            if not mixed:
+                xp[sslc[b]] += zp[sslc[b]]
     d, dp = z.copy(), zp.copy()
     for k in range(maxit):
         if done.all():
@@ -139,13 +190,19 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000):
             nr = np.linalg.norm(r[sl])
             if nr / r0[b] <= tol or nr <= 1e-14 * scale[b] or rz <= 1e-24 * rho0[b]:
                 done[b] = True
-                xp[ss] += zp_new[ss]
+                if not mixed:
+                    xp[ss] += zp_new[ss]
                 continue
             beta = rz / rho[b]
             betas[b].append(beta)
             rho[b] = rz
             d[sl] = z_new[sl] + beta * d[sl]
             dp[ss] = zp_new[ss] + beta * dp[ss]
+    if mixed:
+        # closing coarse pressure correction with the FP64 basis
+        P64 = [P.P64[P.off_P[s]:P.off_P[s] + m[s] * ng[s]].reshape(m[s], ng[s]) for s in range(ns)]
+        wc = coarse([P64[s] @ (w[s] * r[gl[s]]) for s in range(ns)], np.zeros(ns))
+        xp += np.array([wc[inst[s]][P.inst_ncf[inst[s]] + P.sub_local[s]] for s in range(ns)])
     # post
     flux = np.zeros(int(P.inst_nfaces.sum()))
     pres = np.zeros(int(P.inst_ncells.sum()))

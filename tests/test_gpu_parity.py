@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Element-wise comparisons of flux and pressure on seeded inputs, iteration
+counts and Lanczos estimates, the Step-3 operator and the BDDC
+preconditioner on random vectors, batching (each instance's result is the
+same alone and in a batch), host versus device buffers, and edge cases.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from synth import make_config  # noqa: E402
+from synth.problems import Grid, Problem, box_partition, irregular_box_partition, \
+    no_flow_bc, pressure_drop_bc  # noqa: E402
+from oracle import BDDCOracle  # noqa: E402
+from parity import FP64_REL, CONVERGED_REL, MIXED_REL, iteration_slack  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bddc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_02090_gb300 import bddc as b
+    return b
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def gpu_solve(bddc, pbs, tol, tau=None, precision=0, device_io=True, maxit=5000, check=True):
+    opt = bddc.default_options(tau=tau or 0.0, precision=precision, maxit=maxit)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = bddc.setup(pbs, opt, stream=stream)
+    f = np.concatenate([pb.f for pb in pbs])
+    bc = np.concatenate([pb.bc_value for pb in pbs])
+    nf, nc = len(bc), len(f)
+    if device_io:
+        flux = torch.empty(nf, dtype=torch.float64, device="cuda")
+        pres = torch.empty(nc, dtype=torch.float64, device="cuda")
+        its = torch.empty(len(pbs), dtype=torch.int32, device="cuda")
+        rc = h.solve(_dev(f), _dev(bc), tol, flux, pres, its, check=check)
+        torch.cuda.synchronize()
+        out = flux.cpu().numpy(), pres.cpu().numpy(), its.cpu().numpy()
+    else:
+        flux = np.empty(nf)
+        pres = np.empty(nc)
+        its = np.empty(len(pbs), dtype=np.int32)
+        rc = h.solve(f, bc, tol, flux, pres, its, check=check)
+        out = flux, pres, its
+    stats = [h.stats(i) for i in range(len(pbs))]
+    h.close()
+    return out + (stats, rc)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _wells(pb, pure_flux=False):
+    pb.f = np.zeros(pb.grid.n_cells)
+    pb.f[0] = 1.0 / pb.grid.cell_volume
+    pb.f[-1] = -1.0 / pb.grid.cell_volume
+    if pure_flux:
+        pb.bc_type, pb.bc_value = no_flow_bc(pb.grid)
+    return pb
+
+
+def _irregular2d():
+    g = Grid(2, (23, 17, 1), (2.0, 1.0, 1.0))
+    rng = np.random.default_rng(5)
+    perm = 10 ** rng.normal(0, 1.0, g.n_cells)
+    t, v = pressure_drop_bc(g, 2.0, -1.0)
+    return Problem("irr", g, perm, irregular_box_partition(g, 11), t, v, np.zeros(g.n_cells))
+
+
+def _irregular3d():
+    g = Grid(3, (11, 9, 7), (1.0, 2.0, 0.5))
+    rng = np.random.default_rng(9)
+    perm = 10 ** rng.normal(0, 1.0, (g.n_cells, 3))
+    t, v = pressure_drop_bc(g)
+    return Problem("irr3", g, perm, irregular_box_partition(g, 4), t, v, np.zeros(g.n_cells))
+
+
+CASES = {
+    "c1": lambda: make_config("c1"),
+    "c1_wells_pure_flux": lambda: _wells(make_config("c1"), pure_flux=True),
+    "tiny3d": lambda: make_config("tiny3d"),
+    "irregular2d": _irregular2d,
+    "irregular3d_anisotropic": _irregular3d,
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("tau", [None, 4.0])
+def test_fp64_solve_matches_oracle(bddc, case, tau):
+    pb = CASES[case]()
+    o = BDDCOracle(pb, tau=tau)
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, tau)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= max(FP64_REL, 1e-8 * ref.kappa)
+    assert _rel(pres, ref.pressure) <= max(FP64_REL, 1e-8 * ref.kappa)
+    assert abs(st[0].kappa - ref.kappa) <= 0.02 * ref.kappa
+    # both converged: agreement to ~1e-10
+    ref = o.solve(tol=1e-12)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-12, tau)
+    assert _rel(flux, ref.flux) <= CONVERGED_REL
+    assert _rel(pres, ref.pressure) <= CONVERGED_REL
+    if tau is not None:
+        assert np.isclose(st[0].omega_tilde, o.omega_tilde, rtol=1e-8)
+        assert st[0].n_coarse == o.n_coarse
+
+
+@pytest.mark.parametrize("tau,seed", [(10.0, 2090), (100.0, 2090), (10.0, 2136)])
+def test_channelized_60x220_fp64_and_fp32(bddc, tau, seed):
+    """The 2D 60 x 220 channelized workload (6 x 22 subdomains, contrast ~1e7)
+    at full size: FP64 path within 1e-8 of the oracle, FP32-apply path within
+    1e-6 after the FP64 CG converges to 1e-8, both cellwise conservative."""
+    from oracle.discretization import residuals
+    pb = make_config("c2", seed=seed)
+    o = BDDCOracle(pb, tau=tau)
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, tau, precision=bddc.BDDC_PREC_FP64)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    # two solutions with relative residual 1e-8 differ by up to ~kappa * 1e-8
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    assert abs(st[0].kappa - ref.kappa) <= 0.02 * ref.kappa
+    flux32, pres32, its32, st32, _ = gpu_solve(bddc, [pb], 1e-8, tau, precision=bddc.BDDC_PREC_FP32)
+    assert _rel(flux32, ref.flux) <= MIXED_REL
+    assert _rel(pres32, ref.pressure) <= MIXED_REL
+    for u, p_ in ((flux, pres), (flux32, pres32)):
+        _, r2 = residuals(o.disc, u, p_)
+        assert np.abs(r2).max() <= 1e-11 * np.abs(u).max()
+    # the FP32 preconditioner changes the iteration count (stated, not +-1)
+    assert abs(int(its32[0]) - ref.iterations) <= 2 + int(0.25 * ref.iterations)
+    # converged: FP64 path within 1e-9 of the oracle
+    ref = o.solve(tol=1e-12)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-12, tau, precision=bddc.BDDC_PREC_FP64)
+    assert _rel(flux, ref.flux) <= CONVERGED_REL
+    assert _rel(pres, ref.pressure) <= CONVERGED_REL
+
+
+def test_operator_and_preconditioner_match_oracle(bddc):
+    pb = make_config("c1")
+    o = BDDCOracle(pb, tau=3.0)
+    h = bddc.setup([pb], bddc.default_options(tau=3.0), stream=torch.cuda.current_stream().cuda_stream)
+    _, ng, ns = h.sizes()
+    assert ng == o.ss.n_gamma and ns == o.ss.N
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        u = rng.standard_normal(ng)
+        p0 = rng.standard_normal(ns)
+        q = torch.empty(ng, dtype=torch.float64, device="cuda")
+        h.apply_operator(_dev(u), _dev(p0), q)
+        qo, _ = o.apply_operator(u, p0)
+        assert _rel(q.cpu().numpy(), qo) <= 1e-13
+        r = rng.standard_normal(ng)
+        z = torch.empty(ng, dtype=torch.float64, device="cuda")
+        z0 = torch.empty(ns, dtype=torch.float64, device="cuda")
+        h.apply_preconditioner(_dev(r), z, z0)
+        zo, z0o = o.precondition(r)
+        assert _rel(z.cpu().numpy(), zo) <= 1e-11
+        assert _rel(z0.cpu().numpy(), z0o) <= 1e-9
+    h.close()
+
+
+def test_batched_instances_equal_alone(bddc):
+    """Instances of different sizes in one persistent launch give bit-identical
+    results to their solo solves."""
+    pbs = [make_config("c1"), _irregular2d(), make_config("c1", seed=11), make_config("tiny3d")]
+    flux, pres, its, st, _ = gpu_solve(bddc, pbs, 1e-8, 4.0)
+    fo = np.cumsum([0] + [len(pb.bc_type) for pb in pbs])
+    co = np.cumsum([0] + [pb.grid.n_cells for pb in pbs])
+    for b, pb in enumerate(pbs):
+        fa, pa, ia, _, _ = gpu_solve(bddc, [pb], 1e-8, 4.0)
+        assert its[b] == ia[0]
+        assert np.array_equal(flux[fo[b]:fo[b + 1]], fa)
+        assert np.array_equal(pres[co[b]:co[b + 1]], pa)
+
+
+def test_host_and_device_buffers_agree(bddc):
+    pb = _irregular2d()
+    a = gpu_solve(bddc, [pb], 1e-9, None, device_io=True)
+    b = gpu_solve(bddc, [pb], 1e-9, None, device_io=False)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_subassembled_apply_raw_matches_operator(bddc):
+    pb = make_config("tiny3d")
+    hs = bddc.HostSetup([pb])
+    ng = hs.get("sub_ng")
+    n_sub = len(ng)
+    slot_off = hs.get("off_slot")
+    h = bddc.setup([pb], bddc.default_options(), stream=torch.cuda.current_stream().cuda_stream)
+    _, nG, _ = h.sizes()
+    u = np.random.default_rng(2).standard_normal(nG)
+    q_ref = torch.empty(nG, dtype=torch.float64, device="cuda")
+    h.apply_operator(_dev(u), torch.zeros(n_sub, dtype=torch.float64, device="cuda"), q_ref)
+    q = torch.full((nG,), np.nan, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(int(slot_off[-1]), dtype=torch.float64, device="cuda")
+    bddc.subassembled_apply(n_sub, _dev(ng), _dev(slot_off), _dev(hs.get("off_S")), _dev(hs.get("S")),
+                            _dev(hs.get("slot_g")), _dev(hs.get("slot_partner")), nG, _dev(u), q, scratch)
+    torch.cuda.synchronize()
+    assert not torch.isnan(q).any()
+    assert torch.allclose(q, q_ref, rtol=1e-13, atol=1e-13 * float(q_ref.abs().max()))
+    h.close()
+
+
+def test_edge_cases(bddc):
+    # one subdomain with pressure faces: the interface is the pressure faces
+    g = Grid(2, (8, 6, 1), (1.0, 1.0, 1.0))
+    t, v = pressure_drop_bc(g)
+    rng = np.random.default_rng(3)
+    pb = Problem("one", g, 10 ** rng.normal(0, 1, g.n_cells), np.zeros(g.n_cells, np.int32), t, v,
+                 np.zeros(g.n_cells))
+    ref = BDDCOracle(pb).solve(tol=1e-10)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-10)
+    assert _rel(flux, ref.flux) <= 1e-9 and _rel(pres, ref.pressure) <= 1e-9
+    # constant k: Steps 1-2 are exact, CG has nothing to do
+    g = Grid(2, (12, 12, 1), (1.0, 1.0, 1.0))
+    t, v = pressure_drop_bc(g)
+    pb = Problem("cf", g, np.full(g.n_cells, 2.0), box_partition(g, (3, 3)), t, v, np.zeros(g.n_cells))
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-10)
+    assert its[0] <= 3  # the residual is rounding noise in range(B_0^T)
+    nxf = 13 * 12
+    assert np.allclose(flux[:nxf], 2.0 / 12.0, rtol=1e-11)
+    # iteration limit: status and return code say so, outputs are written
+    pb = make_config("c1")
+    flux, pres, its, st, rc = gpu_solve(bddc, [pb], 1e-12, None, maxit=3, check=False)
+    assert rc == bddc.BDDC_E_NOT_CONVERGED and st[0].status == bddc.BDDC_E_NOT_CONVERGED
+    assert its[0] == 3 and np.all(np.isfinite(flux)) and np.all(np.isfinite(pres))
+    # invalid input is rejected before any GPU work
+    bad = make_config("c1")
+    bad.perm = bad.perm.copy()
+    bad.perm[0] = np.nan
+    with pytest.raises(bddc.BDDCError) as e:
+        bddc.setup([bad])
+    assert e.value.code == bddc.BDDC_E_PERM
