@@ -191,7 +191,7 @@ int bddc_last_solve_timing(const bddc_handle* h, double* kernel_ms, double* algo
  *           inst_s0 inst_s1 inst_face_off inst_nfaces inst_cell_off
  *           inst_ncells off_S off_F off_P off_Gpre off_Gpost off_slot
  *           off_cslot off_cell off_int cell_gid int_fid g_fid
- *   double: inst_vol inst_omega sub_d slot_w slot_dsig slot_coef g_bsign S F P Gpre
+ *   double: inst_vol inst_omega sub_d slot_w slot_dsig slot_coef slot_fcoefp g_bsign S F P Gpre
  *           Gpost Kinv P64  (F and P are FP64 copies of the operators the
  *           GPU applies, FP32-rounded for FP32 setups; P64 is the FP64 basis)
  * bddc_host_setup_query gives the element count and size (0 count for an
@@ -209,6 +209,15 @@ void bddc_host_setup_destroy(bddc_host_setup* hs);
  * "prhs" "part_rr" "part_rz" "part_dq" (per subdomain).  *count receives
  * the length; dst may be NULL to query it. */
 int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64_t* count);
+
+/* Diagnostic phase timeline of the last solve: pairs (phase id, global
+ * timer in ns) recorded by CTA 0 as each grid-wide phase of the persistent
+ * kernel ended (ids: 0 start, 1 Step-1 restriction, 2 Step-1 coarse solve,
+ * 3 u_0, 4 Step-2 residual, 5 f* and first restriction, 6 coarse solve,
+ * 7 prolongation, 8 direction update and operator, 9 CG update and
+ * restriction, 10-13 closing pressure correction); unused pairs are zero.
+ * *count receives the number of int64 entries; pairs may be NULL. */
+int bddc_debug_phase_times(const bddc_handle* h, int64_t* pairs, int64_t* count);
 
 const char* bddc_last_error(const bddc_handle* h);
 const char* bddc_error_string(int code);

@@ -81,6 +81,7 @@ def _load():
         "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
         "bddc_host_setup_destroy": (None, [P]),
         "bddc_debug_vector": (C.c_int, [P, C.c_char_p, P, P]),
+        "bddc_debug_phase_times": (C.c_int, [P, P, P]),
         "bddc_last_error": (C.c_char_p, [P]),
         "bddc_error_string": (C.c_char_p, [C.c_int]),
         "bddc_destroy": (None, [P]),
@@ -96,7 +97,8 @@ lib = _load()
 EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
-            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_last_error",
+            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_debug_phase_times",
+            "bddc_last_error",
             "bddc_error_string", "bddc_destroy")
 
 
@@ -214,6 +216,19 @@ class Handle:
         out = np.empty(n.value)
         lib.bddc_debug_vector(self._h, name.encode(), out.ctypes.data, None)
         return out
+
+    def phase_times(self):
+        """[(phase id, ns since kernel start)] of the last solve."""
+        n = C.c_int64()
+        lib.bddc_debug_phase_times(self._h, None, C.byref(n))
+        out = np.zeros(n.value, dtype=np.int64)
+        lib.bddc_debug_phase_times(self._h, out.ctypes.data, None)
+        pairs = out.reshape(-1, 2)
+        pairs = pairs[pairs[:, 1] != 0]
+        if len(pairs) == 0:
+            return []
+        t0 = pairs[0, 1]
+        return [(int(a), int(b - t0)) for a, b in pairs]
 
     def last_solve_timing(self):
         ms, by = C.c_double(), C.c_double()

@@ -43,6 +43,7 @@ struct Packed {
     // indexed from the subdomain's slot offset) and, per local coarse slot,
     // the start of its group (-1 for adaptive rows)
     std::vector<int> slot_fperm, cslot_fstart;
+    std::vector<double> slot_fcoefp;  // coefficient of slot_fperm[q], in the same order
     // per local coarse slot: instance-local coarse index
     std::vector<int> cslot_c;
     // per local cell / interior flux: index into the batched output arrays

@@ -99,6 +99,20 @@ __device__ bool grid_barrier(GridSync* gs) {
     return ok_sh != 0;
 }
 
+// grid barrier that also records, on CTA 0, the phase that just ended and
+// the global timer (ns) when the barrier released
+__device__ __forceinline__ bool phase_end(const Params& p, int phase, int& nts) {
+    const bool ok = grid_barrier(p.gsync);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.tstamp && nts < p.tstamp_cap) {
+        long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        p.tstamp[2 * nts] = phase;
+        p.tstamp[2 * nts + 1] = t;
+        ++nts;
+    }
+    return ok;
+}
+
 // contiguous chunk of U units for this CTA / this warp
 __device__ __forceinline__ void cta_range(int64_t U, int64_t& a, int64_t& b) {
     a = (U * (int64_t)blockIdx.x) / gridDim.x;
@@ -118,7 +132,7 @@ struct PrecFP64 {
     static constexpr bool kMixed = false;
 };
 struct PrecMixed {
-    using S_t = double;   // the operator stays FP64: it defines the problem
+    using S_t = float2;   // the operator as an FP32 pair (48 significant bits)
     using F_t = float;
     static constexpr bool kMixed = true;
 };
@@ -151,6 +165,12 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     c.w.wcs = c.w.xin + p.max_in_post;
     c.w.tsum = c.w.wcs + p.max_m + 1;
     return c;
+}
+
+// stage x[0..n) as FP32 (hi only: inputs of the FP32 operators)
+__device__ __forceinline__ void split_hi(WarpSm& w, int n) {
+    for (int k = threadIdx.x & 31; k < n; k += 32) w.xh[k] = __double2float_rn(w.x[k]);
+    __syncwarp();
 }
 
 // stage x[0..n) from the warp's x into the FP32 pair representation
@@ -217,23 +237,36 @@ __device__ __forceinline__ double gemv_out_f(const double* __restrict__ M, int n
     return gemv_out(M, n_out, n_in, w, o);
 }
 
-// restriction rc_a = sum_k P[a*ng + k] x[k] (warp dot per row a)
+// restriction rc_a = sum_k P[a*ng + k] x[k]: lane per row a, walking its
+// contiguous row (consecutive loads of one lane share cache lines); all
+// loads are independent, so one pass costs about one memory latency
 __device__ __forceinline__ void restrict_rows(const double* __restrict__ P, int m, int ng, const WarpSm& w, double* out) {
-    const int l = threadIdx.x & 31;
-    for (int a = 0; a < m; ++a) {
-        double acc = 0.0;
-        for (int k = l; k < ng; k += 32) acc = fma(__ldg(P + (int64_t)a * ng + k), w.x[k], acc);
-        acc = warp_sum(acc);
-        if (l == 0) out[a] = acc;
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        const double* row = P + (int64_t)a * ng;
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+#pragma unroll 4
+        for (; k + 1 < ng; k += 2) {
+            a0 = fma(__ldg(row + k), w.x[k], a0);
+            a1 = fma(__ldg(row + k + 1), w.x[k + 1], a1);
+        }
+        if (k < ng) a0 = fma(__ldg(row + k), w.x[k], a0);
+        out[a] = a0 + a1;
     }
 }
-__device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m, int ng, const WarpSm& w, double* out) {
-    const int l = threadIdx.x & 31;
-    for (int a = 0; a < m; ++a) {
-        float acc = 0.0f;
-        for (int k = l; k < ng; k += 32) acc = fmaf(__ldg(P + (int64_t)a * ng + k), w.xh[k], acc);
-        const double d = warp_sum((double)acc);
-        if (l == 0) out[a] = d;
+__device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m, int ng, const WarpSm& w, double* out,
+                                              const double* add = nullptr) {
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        const float* row = P + (int64_t)a * ng;
+        float a0 = 0.0f, a1 = 0.0f;
+        int k = 0;
+#pragma unroll 4
+        for (; k + 1 < ng; k += 2) {
+            a0 = fmaf(__ldg(row + k), w.xh[k], a0);
+            a1 = fmaf(__ldg(row + k + 1), w.xh[k + 1], a1);
+        }
+        if (k < ng) a0 = fmaf(__ldg(row + k), w.xh[k], a0);
+        out[a] = (double)(a0 + a1) + (add ? add[a] : 0.0);
     }
 }
 
@@ -257,7 +290,8 @@ __device__ __forceinline__ double prolong_out(const float* __restrict__ P, int m
 // and the preconditioner output keeps exact face net fluxes, so it stays
 // balanced (Sec. 3) to FP64 rounding.
 //
-// t[a] = sum over the dofs of net-flux row a of coef * v (lane per row)
+// t[a] = (sum over the dofs of net-flux row a of coef * v) / (dofs of a),
+// lane per row; 0 for adaptive rows
 __device__ __forceinline__ void face_sums(const Params& p, int64_t s, const double* v, double* t) {
     const int m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -265,11 +299,10 @@ __device__ __forceinline__ void face_sums(const Params& p, int64_t s, const doub
         const int na = p.cslot_n[co + a];
         double acc = 0.0;
         if (na > 0) {
-            const int fs = p.cslot_fstart[co + a];
-            for (int q = 0; q < na; ++q) {
-                const int k = p.slot_fperm[so + fs + q];
-                acc += p.slot_coef[so + k] * v[k];
-            }
+            const int64_t fs = so + p.cslot_fstart[co + a];
+#pragma unroll 4
+            for (int q = 0; q < na; ++q) acc += __ldg(p.slot_fcoefp + fs + q) * v[__ldg(p.slot_fperm + fs + q)];
+            acc /= (double)na;
         }
         t[a] = acc;
     }
@@ -278,22 +311,21 @@ __device__ __forceinline__ void face_sums(const Params& p, int64_t s, const doub
 // v <- P_Z v
 __device__ __forceinline__ void remove_face_flux(const Params& p, int64_t s, double* v, const double* t) {
     const int ng = p.sub_ng[s];
-    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
-    for (int k = threadIdx.x & 31; k < ng; k += 32) {
-        const int a = p.slot_fcs[so + k];
-        v[k] -= p.slot_coef[so + k] * t[a] / (double)p.cslot_n[co + a];
-    }
+    const int64_t so = p.off_slot[s];
+    for (int k = threadIdx.x & 31; k < ng; k += 32) v[k] -= p.slot_coef[so + k] * t[p.slot_fcs[so + k]];
     __syncwarp();
 }
 // v <- P_Z v + Psi_0 wcs
-__device__ __forceinline__ void set_face_flux(const Params& p, int64_t s, double* v, const double* t,
-                                              const double* wcs) {
+__device__ __forceinline__ void set_face_flux(const Params& p, int64_t s, double* v, double* t, const double* wcs) {
+    const int m = p.sub_m[s];
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
-    for (int k = threadIdx.x & 31; k < ng; k += 32) {
-        const int a = p.slot_fcs[so + k];
-        v[k] += p.slot_coef[so + k] * (wcs[a] - t[a]) / (double)p.cslot_n[co + a];
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        const int na = p.cslot_n[co + a];
+        if (na > 0) t[a] = wcs[a] / (double)na - t[a];
     }
+    __syncwarp();
+    for (int k = threadIdx.x & 31; k < ng; k += 32) v[k] += p.slot_coef[so + k] * t[p.slot_fcs[so + k]];
     __syncwarp();
 }
 
@@ -317,14 +349,9 @@ __device__ void restrict_apply(const Params& p, int64_t s, WarpSm& w) {
         // rc = Psi_0^T r + Psi^T P_Z r ; y = P_Z F P_Z r
         face_sums(p, s, w.x, w.tsum);
         remove_face_flux(p, s, w.x, w.tsum);
-        split_pairs(w, ng);
-        restrict_rows(P, m, ng, w, p.rcl + co);
+        split_hi(w, ng);
+        restrict_rows(P, m, ng, w, p.rcl + co, w.tsum);  // tsum is 0 on adaptive rows
         __syncwarp();
-        if ((threadIdx.x & 31) == 0)
-            for (int a = 0; a < m; ++a) {
-                const int na = p.cslot_n[co + a];
-                if (na > 0) p.rcl[co + a] += w.tsum[a] / (double)na;
-            }
         for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = gemv_out_f(F, ng, ng, w, k);
         __syncwarp();
         face_sums(p, s, w.xin, w.tsum);
@@ -372,6 +399,7 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
     const int64_t ncn = p.inst_ncn[b], ncf = p.inst_ncf[b], coff = p.inst_coff[b];
     const int64_t cfo = p.inst_cfoff[b];
     const int64_t ncols = step1 ? ncn : ncf;
+    float2* rhs2 = reinterpret_cast<float2*>(rhs);  // mixed: the rhs as FP32 pairs
     if (staged != b) {
         __syncthreads();
         const int64_t s0 = p.inst_s0[b];
@@ -383,7 +411,12 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
             } else {
                 v = __ldcg(p.prhs + s0 + (c - ncf));
             }
-            rhs[c] = v;
+            if constexpr (PR::kMixed) {
+                const float hi = __double2float_rn(v);
+                rhs2[c] = make_float2(hi, __double2float_rn(v - (double)hi));
+            } else {
+                rhs[c] = v;
+            }
         }
         __syncthreads();
         staged = b;
@@ -399,9 +432,8 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
             float sh = 0.0f, sl = 0.0f;
             for (int64_t c = l; c < ncols; c += 32) {
                 const float2 a = __ldg(kr + c);
-                const double xv = rhs[c];
-                const float xh = __double2float_rn(xv);
-                const float xl = __double2float_rn(xv - (double)xh);
+                const float2 xv = rhs2[c];
+                const float xh = xv.x, xl = xv.y;
                 const float pr = __fmul_rn(a.x, xh);
                 float e = __fmaf_rn(a.x, xh, -pr);
                 e = __fmaf_rn(a.x, xl, e);
@@ -455,6 +487,7 @@ __device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
     }
     for (int r = l; r < nc; r += 32) w.xin[r] = p.f_in[p.cell_gid[cb + r]];
     __syncwarp();
+    if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     const double* G = p.Gpre + p.off_Gpre[s];
     for (int k = l; k < ng; k += 32) {
@@ -631,6 +664,7 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache
     const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
     if (l == 0) dpnew[s] = dpn;
     __syncwarp();
+    if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     double dq = 0.0;
     for (int kk = l; kk < ng; kk += 32) {
@@ -754,66 +788,74 @@ __device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
 
 // ---- the persistent solve kernel -------------------------------------------------------
 template <class PR>
-__global__ void __launch_bounds__(kThreads) bddc_solve_kernel(Params p) {
+__global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     extern __shared__ double smem_base[];
     CtaSm sm = carve(p, smem_base);
     WarpSm& w = sm.w;
     int64_t a, e;
     int staged;
+    int nts = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.tstamp && p.tstamp_cap > 0) {
+        long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        p.tstamp[0] = 0;
+        p.tstamp[1] = t;
+        nts = 1;
+    }
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) ph_step1<PR>(p, s, w);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 1, nts)) return;
     staged = -1;
     cta_range(p.n_cunits, a, e);
     for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 2, nts)) return;
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) ph_u0<PR>(p, s, w);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 3, nts)) return;
     for (int64_t s = a; s < e; ++s) ph_step2<PR>(p, s, w);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 4, nts)) return;
     for (int64_t s = a; s < e; ++s) ph_fstar<PR>(p, s, w);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 5, nts)) return;
     staged = -1;
     cta_range(p.n_cunits, a, e);
     for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 6, nts)) return;
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
-    if (!grid_barrier(p.gsync)) return;
+    if (!phase_end(p, 7, nts)) return;
     for (int k = 0;; ++k) {
         InstCache cache;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) ph_dirop<PR>(p, s, k, w, cache);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 8, nts)) return;
         if (__ldcg(p.n_active) <= 0) break;
         cache = InstCache();
         for (int64_t s = a; s < e; ++s) ph_update<PR>(p, s, k, w, cache);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 9, nts)) return;
         staged = -1;
         cta_range(p.n_cunits, a, e);
         for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 6, nts)) return;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 7, nts)) return;
     }
     if constexpr (PR::kMixed) {
         // closing FP64 coarse pressure correction (every instance is done;
         // the coarse phase runs in step-1 layout with a zero pressure part)
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) ph_final_restrict(p, s, w);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 10, nts)) return;
         cta_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) if (threadIdx.x == 0) p.prhs[s] = 0.0;
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 11, nts)) return;
         staged = -1;
         cta_range(p.n_cunits, a, e);
         for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 12, nts)) return;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) ph_final_pressure(p, s);
-        if (!grid_barrier(p.gsync)) return;
+        if (!phase_end(p, 13, nts)) return;
     }
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) ph_post(p, s, w);
@@ -832,6 +874,7 @@ __global__ void __launch_bounds__(kThreads) k_operator_local(Params p, const dou
         const int64_t so = p.off_slot[s];
         for (int k = threadIdx.x & 31; k < ng; k += 32) w.x[k] = u[p.slot_g[so + k]];
         __syncwarp();
+        if constexpr (PR::kMixed) split_pairs(w, ng);
         const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
         const double pv = p0[s];
         for (int k = threadIdx.x & 31; k < ng; k += 32)
@@ -1087,12 +1130,12 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0);
     UP(Gpre, P.Gpre); UP(Gpost, P.Gpost); UP(P64, P.P64);
     UP(slot_fcs, P.slot_fcs); UP(cslot_n, P.cslot_n); UP(slot_coef, P.slot_coef);
-    UP(slot_fperm, P.slot_fperm); UP(cslot_fstart, P.cslot_fstart);
+    UP(slot_fperm, P.slot_fperm); UP(cslot_fstart, P.cslot_fstart); UP(slot_fcoefp, P.slot_fcoefp);
     UP(inst_cfoff, h->inst_cfoff);
 #undef UP
     if (!rc) {
         if (opt.precision == BDDC_PREC_FP32) {
-            // the coarse inverse as FP32 pairs (hi, lo); F and Psi FP32; S FP64
+            // S and the coarse inverse as FP32 pairs (hi, lo); F and Psi FP32
             auto pairs = [](const std::vector<double>& v) {
                 std::vector<float2> o(v.size());
                 for (size_t q = 0; q < v.size(); ++q) {
@@ -1102,15 +1145,14 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
                 return o;
             };
             const float *f = nullptr, *pp = nullptr;
-            const float2* k2 = nullptr;
-            const double* s64 = nullptr;
+            const float2 *k2 = nullptr, *s2 = nullptr;
             rc = upload(h, P.F32, &f);
             if (!rc) rc = upload(h, P.P32, &pp);
-            if (!rc) rc = upload(h, P.S, &s64);
+            if (!rc) rc = upload(h, pairs(P.S), &s2);
             if (!rc) rc = upload(h, pairs(P.Kinv), &k2);
             p.F = f;
             p.P = pp;
-            p.S = s64;
+            p.S = s2;
             p.Kinv = k2;
         } else {
             const double *f = nullptr, *s64 = nullptr, *k64 = nullptr;
@@ -1134,6 +1176,8 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     AL(part_dq, NS); AL(part_rr, NS); AL(part_rz, NS); AL(part_a1, NS); AL(part_a2, NS);
     AL(st, n_instances); AL(alpha_hist, H); AL(beta_hist, H); AL(rho_hist, H);
     AL(n_active, 1); AL(gsync, 1);
+    p.tstamp_cap = 16 + 4 * (opt.maxit + 2);
+    AL(tstamp, 2 * (size_t)p.tstamp_cap);
 #undef AL
     if (rc) {
         bddc_destroy(h);
@@ -1237,6 +1281,7 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     cudaMemsetAsync(p.flux_out, 0, nface * sizeof(double), st);
     cudaMemsetAsync(p.st, 0, sizeof(InstState) * h->n_inst, st);
     cudaMemsetAsync(p.gsync, 0, sizeof(GridSync), st);
+    cudaMemsetAsync(p.tstamp, 0, 2 * sizeof(long long) * (size_t)p.tstamp_cap, st);
     cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);
     void* args[] = {&p};
     const void* kfn = h->precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<PrecMixed>
@@ -1329,6 +1374,15 @@ int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64
     if (dst && len) {
         if (cudaMemcpy(dst, src, len * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
     }
+    return BDDC_OK;
+}
+
+int bddc_debug_phase_times(const bddc_handle* h, int64_t* pairs, int64_t* count) {
+    if (!h) return BDDC_E_INVALID_ARG;
+    const int64_t n = 2 * (int64_t)h->prm.tstamp_cap;
+    if (count) *count = n;
+    if (pairs && cudaMemcpy(pairs, h->prm.tstamp, n * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return BDDC_E_CUDA;
     return BDDC_OK;
 }
 

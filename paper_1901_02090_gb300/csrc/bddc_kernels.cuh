@@ -15,12 +15,11 @@
 // Psi^T r is a warp dot product over a contiguous row of PsiT.
 //
 // Two precisions: FP64 everywhere (S, F, Psi, coarse inverse), or the mixed
-// path where the preconditioner is cheaper: F and Psi in FP32 and the coarse
-// inverse stored as FP32 pairs (hi + lo, 48 significant bits) applied with
-// compensated FP32 arithmetic (FP64 arithmetic on GB300 runs at about 1/64
-// of the FP32 rate).  The operator S stays FP64 in both paths.  The mixed
-// path keeps the preconditioner output exactly balanced (a per-face net-flux
-// correction) and ends with an FP64 coarse pressure correction.
+// path: F and Psi in FP32, and S and the coarse inverse stored as FP32 pairs
+// (hi + lo, 48 significant bits) applied with compensated FP32 arithmetic,
+// since FP64 arithmetic on GB300 runs at about 1/64 of the FP32 rate.  The
+// mixed path keeps the preconditioner symmetric and its output exactly
+// balanced, and ends with an FP64 coarse pressure correction.
 #pragma once
 
 #include <cstdint>
@@ -66,14 +65,15 @@ struct Params {
     const int *slot_fcs, *cslot_n;   // net-flux row of each slot; dofs per net-flux row
     const double* slot_coef;
     const int *slot_fperm, *cslot_fstart;  // slots grouped by net-flux row
+    const double* slot_fcoefp;             // their coefficients, same order
     const int64_t *cell_gid, *int_fid, *g_fid;
     const double* g_bsign;
     const int *c_slot_a, *c_slot_b;
     // coarse units
     int64_t n_cunits;
     const int *cunit_inst, *cunit_row0;
-    // matrices: S is double; Kinv is double (FP64 path) or float2 pairs
-    // (mixed); F and P are double or float; P64 is always FP64
+    // matrices: S and Kinv are double (FP64 path) or float2 pairs (mixed);
+    // F and P are double or float; P64 is always FP64
     const void *S, *F, *P, *Kinv;
     const double *P64, *Gpre, *Gpost;
     // work vectors
@@ -87,6 +87,9 @@ struct Params {
     double *alpha_hist, *beta_hist, *rho_hist;                 // n_inst x (maxit + 1)
     int* n_active;
     GridSync* gsync;
+    // phase timestamps (CTA 0 at each barrier): pairs (phase id, ns)
+    long long* tstamp;
+    int tstamp_cap;
     // io
     const double *f_in, *bc_in;
     double *flux_out, *p_out;

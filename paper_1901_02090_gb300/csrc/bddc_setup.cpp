@@ -1076,7 +1076,11 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                     if (S.rown[a] == 0) { P.cslot_fstart.push_back(-1); continue; }
                     P.cslot_fstart.push_back(start);
                     for (int k = 0; k < S.ng; ++k)
-                        if (S.fcs[k] == a) { P.slot_fperm.push_back(k); ++start; }
+                        if (S.fcs[k] == a) {
+                            P.slot_fperm.push_back(k);
+                            P.slot_fcoefp.push_back(S.fcoef[k]);
+                            ++start;
+                        }
                 }
             }
             for (int a = 0; a < S.m; ++a) {
@@ -1129,7 +1133,7 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
     const std::string n(name ? name : "");
 #define E(x) if (n == #x) return export_vec(P.x, dst, count, eb)
     E(sub_inst); E(sub_ng); E(sub_ni); E(sub_nc); E(sub_m); E(sub_local); E(slot_g); E(slot_partner);
-    E(cslot_c); E(c_slot_a); E(c_slot_b); E(g_slot_a); E(g_slot_b); E(slot_fcs); E(cslot_n); E(slot_coef); E(slot_fperm); E(cslot_fstart);
+    E(cslot_c); E(c_slot_a); E(c_slot_b); E(g_slot_a); E(g_slot_b); E(slot_fcs); E(cslot_n); E(slot_coef); E(slot_fperm); E(cslot_fstart); E(slot_fcoefp);
     E(inst_goff); E(inst_ng); E(inst_coff); E(inst_ncn); E(inst_ncf); E(inst_kinv_off); E(inst_s0); E(inst_s1);
     E(inst_face_off); E(inst_nfaces); E(inst_cell_off); E(inst_ncells); E(off_S); E(off_F); E(off_P);
     E(off_Gpre); E(off_Gpost); E(off_slot); E(off_cslot); E(off_cell); E(off_int); E(cell_gid); E(int_fid); E(g_fid);
