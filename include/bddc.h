@@ -175,6 +175,32 @@ int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset
                             const int* partner, int64_t n_interface, const double* u,
                             double* q, double* slot_scratch, void* stream);
 
+/* Allocation-free variant of bddc_subassembled_apply (the paper has no
+ * counterpart: this is a library-integration entry point).  Some callers
+ * cannot call cudaMalloc: code running where the device allocator is
+ * forbidden or already reserved (inside a caller's memory pool or arena
+ * that owns all device memory, in real-time or safety-certified loops that
+ * allow no allocation after start-up).  This entry point takes the same
+ * inputs and output but no scratch argument: its per-slot scratch is a fixed
+ * array in the library's device memory, BDDC_NOALLOC_MAX_SLOTS doubles
+ * (4 MiB), held by every GPU that loads the library until the process
+ * exits.  It allocates nothing and calls no cudaMalloc or cudaFree.
+ *   - slot_offset[n_sub] larger than BDDC_NOALLOC_MAX_SLOTS is rejected with
+ *     BDDC_E_INVALID_ARG (message from bddc_last_error(NULL));
+ *   - the first call on a device looks up the array's device address on the
+ *     current device (once per device); make that first call before any
+ *     stream capture;
+ *   - every call on a device shares the one array; it needs no clearing
+ *     (each call writes every slot it reads), and calls whose kernels
+ *     overlap on the GPU (different streams, or another host thread) race on
+ *     it: order them on one stream or serialise them.
+ * Device pointers; stream is a cudaStream_t or NULL. */
+#define BDDC_NOALLOC_MAX_SLOTS (1 << 19)
+int bddc_subassembled_apply_noalloc(int n_sub, const int* ng, const int64_t* slot_offset,
+                                    const int64_t* S_offset, const double* S, const int* gidx,
+                                    const int* partner, int64_t n_interface, const double* u,
+                                    double* q, void* stream);
+
 /* Device time (ms) of the last solve's main kernel (the persistent Step 1-3
  * kernel), measured with CUDA events around its launch, and the algorithmic
  * bytes it moved (matrix entries and vectors per iteration times the

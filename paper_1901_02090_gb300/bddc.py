@@ -75,6 +75,7 @@ def _load():
         "bddc_apply_operator": (C.c_int, [P, P, P, P]),
         "bddc_apply_preconditioner": (C.c_int, [P, P, P, P]),
         "bddc_subassembled_apply": (C.c_int, [C.c_int, P, P, P, P, P, P, C.c_int64, P, P, P, P]),
+        "bddc_subassembled_apply_noalloc": (C.c_int, [C.c_int, P, P, P, P, P, P, C.c_int64, P, P, P]),
         "bddc_last_solve_timing": (C.c_int, [P, P, P]),
         "bddc_host_setup_create": (C.c_int, [C.c_int, P, P, P]),
         "bddc_host_setup_query": (C.c_int, [P, C.c_char_p, P, P]),
@@ -96,6 +97,7 @@ def _load():
 lib = _load()
 EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
+            "bddc_subassembled_apply_noalloc",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
             "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_debug_phase_times",
             "bddc_last_error",
@@ -248,6 +250,20 @@ def subassembled_apply(n_sub, ng, slot_offset, S_offset, S, gidx, partner, n_int
                                      _ptr(slot_scratch), None if stream is None else C.c_void_p(int(stream)))
     if rc != BDDC_OK:
         raise BDDCError(rc)
+
+
+NOALLOC_MAX_SLOTS = 1 << 19
+
+
+def subassembled_apply_noalloc(n_sub, ng, slot_offset, S_offset, S, gidx, partner, n_interface, u, q,
+                               stream=None):
+    """bddc_subassembled_apply_noalloc: the same apply with the library's fixed
+    device scratch (no allocation; see include/bddc.h for its limits)."""
+    rc = lib.bddc_subassembled_apply_noalloc(int(n_sub), _ptr(ng), _ptr(slot_offset), _ptr(S_offset), _ptr(S),
+                                             _ptr(gidx), _ptr(partner), int(n_interface), _ptr(u), _ptr(q),
+                                             None if stream is None else C.c_void_p(int(stream)))
+    if rc != BDDC_OK:
+        raise BDDCError(rc, lib.bddc_last_error(None).decode())
 
 
 class HostSetup:

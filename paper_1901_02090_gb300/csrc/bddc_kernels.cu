@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1457,3 +1458,74 @@ int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset
 }
 
 }  // extern "C"
+
+// ---- allocation-free subassembled apply -------------------------------------------
+// The scratch of bddc_subassembled_apply_noalloc: one fixed array of the
+// library's device memory.  Host code never dereferences this name (on the
+// host it is only a stand-in for the symbol); its device address is looked
+// up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[BDDC_NOALLOC_MAX_SLOTS];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// device address of g_noalloc_scratch on the current device (looked up on
+// the first call per device)
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return BDDC_E_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return BDDC_E_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return BDDC_OK;
+}
+}  // namespace
+
+extern "C" int bddc_subassembled_apply_noalloc(int n_sub, const int* ng, const int64_t* slot_offset,
+                                               const int64_t* S_offset, const double* S, const int* gidx,
+                                               const int* partner, int64_t n_interface, const double* u,
+                                               double* q, void* stream) {
+    g_setup_err.clear();
+    if (n_sub <= 0 || !ng || !slot_offset || !S_offset || !S || !gidx || !partner || !u || !q || n_interface <= 0) {
+        g_setup_err = "bddc_subassembled_apply_noalloc: null pointer or non-positive size";
+        return BDDC_E_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t n_slots = 0;
+    if (cudaMemcpy(&n_slots, slot_offset + n_sub, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return BDDC_E_CUDA;
+    if (n_slots < 0 || n_slots > (int64_t)BDDC_NOALLOC_MAX_SLOTS) {
+        g_setup_err = "bddc_subassembled_apply_noalloc: " + std::to_string(n_slots) +
+                      " local slots exceed the fixed scratch of " + std::to_string(BDDC_NOALLOC_MAX_SLOTS) +
+                      " doubles; use bddc_subassembled_apply with caller scratch";
+        return BDDC_E_INVALID_ARG;
+    }
+    std::vector<int> hng(n_sub);
+    if (cudaMemcpy(hng.data(), ng, sizeof(int) * n_sub, cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
+    for (int v : hng)
+        if (v < 0 || v > 1024) {
+            g_setup_err = "bddc_subassembled_apply_noalloc: a local interface size exceeds 1024";
+            return BDDC_E_INVALID_ARG;
+        }
+    double* scratch = nullptr;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc) {
+        g_setup_err = "bddc_subassembled_apply_noalloc: cudaGetSymbolAddress failed";
+        return rc;
+    }
+    k_subassembled_local<<<std::min(n_sub, 4096), 128, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u, scratch);
+    k_assemble<<<(int)std::min<int64_t>((n_slots + 255) / 256, 4096), 256, 0, st>>>(n_slots, scratch, gidx, partner, q);
+    return cudaGetLastError() == cudaSuccess ? BDDC_OK : BDDC_E_CUDA;
+}
