@@ -787,9 +787,12 @@ __device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
     __syncwarp();
 }
 
+#include "bddc_mixed.cuh"
+
 // ---- the persistent solve kernel -------------------------------------------------------
 template <class PR>
 __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
+    constexpr bool MX = PR::kMixed;
     extern __shared__ double smem_base[];
     CtaSm sm = carve(p, smem_base);
     WarpSm& w = sm.w;
@@ -803,63 +806,88 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         p.tstamp[1] = t;
         nts = 1;
     }
+    auto coarse_phase = [&](bool step1) {
+        staged = -1;
+        cta_range(p.n_cunits, a, e);
+        for (int64_t u = a; u < e; ++u) {
+            if constexpr (MX) mx_coarse(p, u, step1, sm.rhs, staged);
+            else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
+        }
+    };
     warp_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_step1<PR>(p, s, w);
+    for (int64_t s = a; s < e; ++s) {
+        if constexpr (MX) mx_step1(p, s, w);
+        else ph_step1<PR>(p, s, w);
+    }
     if (!phase_end(p, 1, nts)) return;
-    staged = -1;
-    cta_range(p.n_cunits, a, e);
-    for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
+    coarse_phase(true);
     if (!phase_end(p, 2, nts)) return;
     warp_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_u0<PR>(p, s, w);
+    for (int64_t s = a; s < e; ++s) {
+        if constexpr (MX) mx_u0(p, s, w);
+        else ph_u0<PR>(p, s, w);
+    }
     if (!phase_end(p, 3, nts)) return;
     for (int64_t s = a; s < e; ++s) ph_step2<PR>(p, s, w);
     if (!phase_end(p, 4, nts)) return;
-    for (int64_t s = a; s < e; ++s) ph_fstar<PR>(p, s, w);
+    for (int64_t s = a; s < e; ++s) {
+        if constexpr (MX) mx_fstar(p, s, w);
+        else ph_fstar<PR>(p, s, w);
+    }
     if (!phase_end(p, 5, nts)) return;
-    staged = -1;
-    cta_range(p.n_cunits, a, e);
-    for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
+    coarse_phase(false);
     if (!phase_end(p, 6, nts)) return;
     warp_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
+    for (int64_t s = a; s < e; ++s) {
+        if constexpr (MX) mx_prolong(p, s, w);
+        else ph_prolong<PR>(p, s, w);
+    }
     if (!phase_end(p, 7, nts)) return;
     for (int k = 0;; ++k) {
         InstCache cache;
         warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_dirop<PR>(p, s, k, w, cache);
+        for (int64_t s = a; s < e; ++s) {
+            if constexpr (MX) mx_dirop(p, s, k, w, cache);
+            else ph_dirop<PR>(p, s, k, w, cache);
+        }
         if (!phase_end(p, 8, nts)) return;
         if (__ldcg(p.n_active) <= 0) break;
         cache = InstCache();
-        for (int64_t s = a; s < e; ++s) ph_update<PR>(p, s, k, w, cache);
+        for (int64_t s = a; s < e; ++s) {
+            if constexpr (MX) mx_update(p, s, k, w, cache);
+            else ph_update<PR>(p, s, k, w, cache);
+        }
         if (!phase_end(p, 9, nts)) return;
-        staged = -1;
-        cta_range(p.n_cunits, a, e);
-        for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, false, sm.rhs, staged);
+        coarse_phase(false);
         if (!phase_end(p, 6, nts)) return;
         warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_prolong<PR>(p, s, w);
+        for (int64_t s = a; s < e; ++s) {
+            if constexpr (MX) mx_prolong(p, s, w);
+            else ph_prolong<PR>(p, s, w);
+        }
         if (!phase_end(p, 7, nts)) return;
     }
-    if constexpr (PR::kMixed) {
+    if constexpr (MX) {
         // closing FP64 coarse pressure correction (every instance is done;
         // the coarse phase runs in step-1 layout with a zero pressure part)
         warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_final_restrict(p, s, w);
+        for (int64_t s = a; s < e; ++s) mx_final_restrict(p, s, w);
         if (!phase_end(p, 10, nts)) return;
         cta_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) if (threadIdx.x == 0) p.prhs[s] = 0.0;
+        for (int64_t s = a; s < e; ++s)
+            if (threadIdx.x == 0) p.prhs[s] = 0.0;
         if (!phase_end(p, 11, nts)) return;
-        staged = -1;
-        cta_range(p.n_cunits, a, e);
-        for (int64_t u = a; u < e; ++u) ph_coarse<PR>(p, u, true, sm.rhs, staged);
+        coarse_phase(true);
         if (!phase_end(p, 12, nts)) return;
         warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) ph_final_pressure(p, s);
+        for (int64_t s = a; s < e; ++s) mx_final_pressure(p, s);
         if (!phase_end(p, 13, nts)) return;
     }
     warp_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) ph_post(p, s, w);
+    for (int64_t s = a; s < e; ++s) {
+        if constexpr (MX) mx_post(p, s, w);
+        else ph_post(p, s, w);
+    }
 }
 
 // ---- stand-alone operator / preconditioner kernels (grid-stride over units) --------
@@ -1132,6 +1160,24 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     UP(Gpre, P.Gpre); UP(Gpost, P.Gpost); UP(P64, P.P64);
     UP(slot_fcs, P.slot_fcs); UP(cslot_n, P.cslot_n); UP(slot_coef, P.slot_coef);
     UP(slot_fperm, P.slot_fperm); UP(cslot_fstart, P.cslot_fstart); UP(slot_fcoefp, P.slot_fcoefp);
+    {
+        auto pairs2 = [](const std::vector<double>& v) {
+            std::vector<float2> o(v.size());
+            for (size_t q = 0; q < v.size(); ++q) {
+                const float hi = (float)v[q];
+                o[q] = make_float2(hi, (float)(v[q] - (double)hi));
+            }
+            return o;
+        };
+        std::vector<double> invn(P.cslot_n.size(), 0.0);
+        for (size_t q = 0; q < invn.size(); ++q) invn[q] = P.cslot_n[q] > 0 ? 1.0 / P.cslot_n[q] : 0.0;
+        std::vector<float> cf(P.slot_coef.begin(), P.slot_coef.end()), cfp(P.slot_fcoefp.begin(), P.slot_fcoefp.end());
+        if (!rc) rc = upload(h, pairs2(P.slot_w), &p.slot_w2);
+        if (!rc) rc = upload(h, pairs2(P.slot_dsig), &p.slot_dsig2);
+        if (!rc) rc = upload(h, pairs2(invn), &p.cslot_inv2);
+        if (!rc) rc = upload(h, cf, &p.slot_coef_f);
+        if (!rc) rc = upload(h, cfp, &p.slot_fcoefp_f);
+    }
     UP(inst_cfoff, h->inst_cfoff);
 #undef UP
     if (!rc) {

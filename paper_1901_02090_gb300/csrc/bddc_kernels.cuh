@@ -66,6 +66,9 @@ struct Params {
     const double* slot_coef;
     const int *slot_fperm, *cslot_fstart;  // slots grouped by net-flux row
     const double* slot_fcoefp;             // their coefficients, same order
+    // mixed path: weights, d*sigma and 1/n as FP32 pairs; coefficients as FP32
+    const float2 *slot_w2, *slot_dsig2, *cslot_inv2;
+    const float *slot_coef_f, *slot_fcoefp_f;
     const int64_t *cell_gid, *int_fid, *g_fid;
     const double* g_bsign;
     const int *c_slot_a, *c_slot_b;

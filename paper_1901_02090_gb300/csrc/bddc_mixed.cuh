@@ -1,0 +1,578 @@
+// Mixed-precision phases of the persistent solve kernel (included by
+// bddc_kernels.cu inside namespace bddc, after the FP64 phases).
+//
+// GB300 retires FP64 arithmetic at about 1/64 of the FP32 rate (~1.6 FP64
+// lane operations per clock per SM), so on this path every per-dof quantity
+// of the CG recurrence (x, r, d, q, z and the local slots) is an FP32 pair
+// (hi, lo) -- "double-float", 48 significant bits -- updated with
+// error-free FP32 transformations.  FP64 remains for the per-instance
+// scalars (alpha, beta, norms), the once-per-solve Step 1/2 and
+// post-processing, and the closing coarse pressure correction.  The
+// subdomain correction F and the coarse basis Psi are FP32 operators applied
+// as P_Z F P_Z and Psi_0 + P_Z Psi (symmetric, exactly balanced), S and the
+// coarse inverse are FP32 pairs.
+#pragma once
+
+// ---- double-float arithmetic (FP32 pairs) -------------------------------------------
+// All operations use explicitly rounded intrinsics so that no FMA contraction
+// changes the error-free transformations.
+__device__ __forceinline__ float2 dd_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 dd_quick(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
+    const float2 s = dd_two_sum(a.x, b.x);
+    return dd_quick(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 dd_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dd_sub(float2 a, float2 b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ float2 dd_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return dd_quick(p, e);
+}
+// a * sign, sign = +1 or -1 (exact)
+__device__ __forceinline__ float2 dd_sign(float2 a, float sgn) { return sgn > 0.0f ? a : dd_neg(a); }
+__device__ __forceinline__ float2 dd_of(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double dd_dbl(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 dd_zero() { return make_float2(0.0f, 0.0f); }
+// xor-butterfly sum: dd_add is commutative, so every lane gets the same bits
+__device__ __forceinline__ float2 dd_warp_sum(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+        v = dd_add(v, t);
+    }
+    return v;
+}
+
+// views of the work buffers as FP32 pairs (same 8-byte slots)
+__device__ __forceinline__ float2* V2(double* p) { return reinterpret_cast<float2*>(p); }
+
+// S (FP32 pairs, input-major) times the pair vector (w.xh, w.xl) for output o
+__device__ __forceinline__ float2 mx_gemv_S(const float2* __restrict__ M, int n, const WarpSm& w, int o) {
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) {
+        const float2 a = __ldg(M + (int64_t)j * n + o);
+        const float xh = w.xh[j], xl = w.xl[j];
+        const float pr = __fmul_rn(a.x, xh);
+        float e = __fmaf_rn(a.x, xh, -pr);
+        e = __fmaf_rn(a.x, xl, e);
+        e = __fmaf_rn(a.y, xh, e);
+        const float t = __fadd_rn(sh, pr);
+        const float bp = __fsub_rn(t, sh);
+        const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(err, e));
+    }
+    return dd_quick(sh, sl);
+}
+
+// face means of a pair vector (vh, vl): t_a = (sum_{k in a} coef_k v_k) / n_a
+// for net-flux rows a, 0 for adaptive rows (lane per row)
+__device__ __forceinline__ void mx_face_means(const Params& p, int64_t s, const float* vh, const float* vl,
+                                              float2* t) {
+    const int m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        const int na = p.cslot_n[co + a];
+        float2 acc = dd_zero();
+        if (na > 0) {
+            const int64_t fs = so + p.cslot_fstart[co + a];
+            for (int q = 0; q < na; ++q) {
+                const int k = __ldg(p.slot_fperm + fs + q);
+                acc = dd_add(acc, dd_sign(make_float2(vh[k], vl[k]), __ldg(p.slot_fcoefp_f + fs + q)));
+            }
+            acc = dd_mul(acc, __ldg(p.cslot_inv2 + co + a));
+        }
+        t[a] = acc;
+    }
+    __syncwarp();
+}
+
+// local part of Algorithm 2 for the weighted residual held in (w.xh, w.xl):
+// rc = Psi_0^T r + Psi^T P_Z r, y = P_Z F P_Z r
+__device__ void mx_restrict(const Params& p, int64_t s, WarpSm& w) {
+    const int ng = p.sub_ng[s], m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const int l = threadIdx.x & 31;
+    float2* t = V2(w.tsum);
+    float2* y = V2(w.xin);
+    mx_face_means(p, s, w.xh, w.xl, t);
+    for (int k = l; k < ng; k += 32) {
+        const float2 v = dd_sub(make_float2(w.xh[k], w.xl[k]),
+                                dd_sign(t[p.slot_fcs[so + k]], __ldg(p.slot_coef_f + so + k)));
+        w.xh[k] = v.x;
+        w.xl[k] = v.y;
+    }
+    __syncwarp();
+    const float* P = reinterpret_cast<const float*>(p.P) + p.off_P[s];
+    const float* F = reinterpret_cast<const float*>(p.F) + p.off_F[s];
+    float2* rcl = V2(p.rcl);
+    for (int a = l; a < m; a += 32) {
+        const float* row = P + (int64_t)a * ng;
+        float a0 = 0.0f, a1 = 0.0f;
+        int k = 0;
+#pragma unroll 4
+        for (; k + 1 < ng; k += 2) {
+            a0 = fmaf(__ldg(row + k), w.xh[k], a0);
+            a1 = fmaf(__ldg(row + k + 1), w.xh[k + 1], a1);
+        }
+        if (k < ng) a0 = fmaf(__ldg(row + k), w.xh[k], a0);
+        rcl[co + a] = dd_add(make_float2(a0 + a1, 0.0f), t[a]);
+    }
+    for (int o = l; o < ng; o += 32) {
+        float a0 = 0.0f, a1 = 0.0f;
+        int j = 0;
+#pragma unroll 4
+        for (; j + 1 < ng; j += 2) {
+            a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
+            a1 = fmaf(__ldg(F + (int64_t)(j + 1) * ng + o), w.xh[j + 1], a1);
+        }
+        if (j < ng) a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
+        y[o] = make_float2(a0 + a1, 0.0f);
+    }
+    __syncwarp();
+    // P_Z on y (face means of y; y's low parts are zero)
+    for (int a = l; a < m; a += 32) {
+        const int na = p.cslot_n[co + a];
+        float2 acc = dd_zero();
+        if (na > 0) {
+            const int64_t fs = so + p.cslot_fstart[co + a];
+            for (int q = 0; q < na; ++q)
+                acc = dd_add(acc, dd_sign(y[__ldg(p.slot_fperm + fs + q)], __ldg(p.slot_fcoefp_f + fs + q)));
+            acc = dd_mul(acc, __ldg(p.cslot_inv2 + co + a));
+        }
+        t[a] = acc;
+    }
+    __syncwarp();
+    float2* yl = V2(p.yl);
+    for (int k = l; k < ng; k += 32)
+        yl[so + k] = dd_sub(y[k], dd_sign(t[p.slot_fcs[so + k]], __ldg(p.slot_coef_f + so + k)));
+    __syncwarp();
+}
+
+// v = Psi_0 wcs + P_Z Psi wcs for the staged coarse values (w.wcs as pairs);
+// the result is left in (w.xh, w.xl)
+__device__ void mx_prolong_local(const Params& p, int64_t s, WarpSm& w) {
+    const int ng = p.sub_ng[s], m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const int l = threadIdx.x & 31;
+    const float2* wcs = V2(w.wcs);
+    float2* t = V2(w.tsum);
+    const float* P = reinterpret_cast<const float*>(p.P) + p.off_P[s];
+    for (int k = l; k < ng; k += 32) {
+        float acc = 0.0f;
+        for (int a = 0; a < m; ++a) acc = fmaf(__ldg(P + (int64_t)a * ng + k), wcs[a].x, acc);
+        w.xh[k] = acc;
+        w.xl[k] = 0.0f;
+    }
+    __syncwarp();
+    mx_face_means(p, s, w.xh, w.xl, t);
+    // per row: u_a = wcs_a / n_a - mean_a
+    for (int a = l; a < m; a += 32)
+        if (p.cslot_n[co + a] > 0) t[a] = dd_sub(dd_mul(wcs[a], __ldg(p.cslot_inv2 + co + a)), t[a]);
+    __syncwarp();
+    for (int k = l; k < ng; k += 32) {
+        const float2 v = dd_add(make_float2(w.xh[k], w.xl[k]),
+                                dd_sign(t[p.slot_fcs[so + k]], __ldg(p.slot_coef_f + so + k)));
+        w.xh[k] = v.x;
+        w.xl[k] = v.y;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void mx_stage_wc(const Params& p, int64_t s, const float2* wc_b, WarpSm& w) {
+    const int m = p.sub_m[s];
+    const int64_t co = p.off_cslot[s];
+    float2* wcs = V2(w.wcs);
+    for (int a = threadIdx.x & 31; a < m; a += 32) wcs[a] = __ldcg(wc_b + p.cslot_c[co + a]);
+    __syncwarp();
+}
+
+// ---- phases ------------------------------------------------------------------------------
+__device__ void mx_step1(const Params& p, int64_t s, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    const int ng = p.sub_ng[s], m = p.sub_m[s], nc = p.sub_nc[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const int l = threadIdx.x & 31;
+    for (int k = l; k < ng; k += 32) {
+        const int gi = p.slot_g[so + k];
+        const double sg = p.g_bsign[gi];
+        const double gv = sg != 0.0 ? sg * p.bc_in[p.g_fid[gi]] : 0.0;
+        if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.g[gi] = gv;
+        w.x[k] = p.slot_w[so + k] * gv;
+    }
+    __syncwarp();
+    const double* P64 = p.P64 + p.off_P[s];
+    float2* rcl = V2(p.rcl);
+    for (int a = l; a < m; a += 32) {
+        double acc = 0.0;
+        for (int k = 0; k < ng; ++k) acc = fma(__ldg(P64 + (int64_t)a * ng + k), w.x[k], acc);
+        rcl[co + a] = dd_of(acc);
+    }
+    double v = 0.0;
+    const int64_t cb = p.off_cell[s];
+    for (int r = l; r < nc; r += 32) v += -p.f_in[p.cell_gid[cb + r]];
+    v = warp_sum(v);
+    if (l == 0) p.prhs[s] = p.sub_d[s] * p.inst_vol[b] * v;
+    __syncwarp();
+}
+
+// coarse solve rows (CTA per unit) in FP32-pair arithmetic: wc = Kinv * rhs
+__device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_area, int& staged) {
+    const int b = p.cunit_inst[u];
+    if (!step1 && inst_done_block(p, b)) return;
+    const int64_t ncn = p.inst_ncn[b], ncf = p.inst_ncf[b], coff = p.inst_coff[b];
+    const int64_t cfo = p.inst_cfoff[b];
+    const int64_t ncols = step1 ? ncn : ncf;
+    float2* rhs = V2(rhs_area);
+    const float2* rcl = V2(p.rcl);
+    if (staged != b) {
+        __syncthreads();
+        const int64_t s0 = p.inst_s0[b];
+        for (int64_t c = threadIdx.x; c < ncols; c += kThreads) {
+            float2 v;
+            if (c < ncf) {
+                const int a = p.c_slot_a[cfo + c], bb = p.c_slot_b[cfo + c];
+                v = a >= 0 ? __ldcg(rcl + a) : dd_zero();
+                if (bb >= 0) v = dd_add(v, __ldcg(rcl + bb));
+            } else {
+                v = dd_of(__ldcg(p.prhs + s0 + (c - ncf)));
+            }
+            rhs[c] = v;
+        }
+        __syncthreads();
+        staged = b;
+    }
+    const float2* K = reinterpret_cast<const float2*>(p.Kinv) + p.inst_kinv_off[b];
+    const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t r0 = p.cunit_row0[u];
+    const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
+    float2* wc = V2(p.wc);
+    for (int64_t row = r0 + wi; row < r1; row += kWarps) {
+        const float2* kr = K + row * ncn;
+        float sh = 0.0f, sl = 0.0f;
+        for (int64_t c = l; c < ncols; c += 32) {
+            const float2 a = __ldg(kr + c);
+            const float2 xv = rhs[c];
+            const float pr = __fmul_rn(a.x, xv.x);
+            float e = __fmaf_rn(a.x, xv.x, -pr);
+            e = __fmaf_rn(a.x, xv.y, e);
+            e = __fmaf_rn(a.y, xv.x, e);
+            const float t = __fadd_rn(sh, pr);
+            const float bp = __fsub_rn(t, sh);
+            const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+            sh = t;
+            sl = __fadd_rn(sl, __fadd_rn(err, e));
+        }
+        const float2 acc = dd_warp_sum(dd_quick(sh, sl));
+        if (l == 0) wc[coff + row] = acc;
+    }
+}
+
+__device__ void mx_u0(const Params& p, int64_t s, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s];
+    mx_stage_wc(p, s, V2(p.wc) + p.inst_coff[b], w);
+    mx_prolong_local(p, s, w);
+    for (int k = threadIdx.x & 31; k < ng; k += 32)
+        p.tl[so + k] = p.slot_w[so + k] * dd_dbl(make_float2(w.xh[k], w.xl[k]));
+    __syncwarp();
+}
+
+// f* (FP64, once per solve), r_0 = f* and x_0 = 0 as pairs, then restrict r_0
+__device__ void mx_fstar(const Params& p, int64_t s, WarpSm& w) {
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s];
+    const int l = threadIdx.x & 31;
+    float2* r0 = V2(p.rbuf0);
+    float2* x = V2(p.x);
+    float2* rl = V2(p.rl);
+    double rr = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int k = l; k < ng; k += 32) {
+        const int pt = p.slot_partner[so + k];
+        const int gi = p.slot_g[so + k];
+        const double gv = __ldcg(p.g + gi);
+        const double loc = __ldcg(p.ql + so + k) + (pt >= 0 ? __ldcg(p.ql + pt) : 0.0);
+        const double fs = gv - loc;
+        if (slot_owner((int)(so + k), pt)) {
+            r0[gi] = dd_of(fs);
+            x[gi] = dd_zero();
+            rr += fs * fs;
+            a1 += gv * gv;
+            a2 += loc * loc;
+        }
+        const float2 wr = dd_of(p.slot_w[so + k] * fs);
+        w.xh[k] = wr.x;
+        w.xl[k] = wr.y;
+        rl[so + k] = wr;
+    }
+    rr = warp_sum(rr);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (l == 0) {
+        p.part_rr[s] = rr;
+        p.part_a1[s] = a1;
+        p.part_a2[s] = a2;
+        p.xp[s] = 0.0;
+        p.dp0[s] = 0.0;
+        p.dp1[s] = 0.0;
+    }
+    __syncwarp();
+    mx_restrict(p, s, w);
+}
+
+__device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    if (inst_done(p, b)) return;
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s];
+    const float2* wcb = V2(p.wc) + p.inst_coff[b];
+    mx_stage_wc(p, s, wcb, w);
+    mx_prolong_local(p, s, w);
+    const float2* yl = V2(p.yl);
+    const float2* rl = V2(p.rl);
+    float2* zl = V2(p.zl);
+    float2 rz = dd_zero();
+    for (int k = threadIdx.x & 31; k < ng; k += 32) {
+        const float2 z = dd_add(make_float2(w.xh[k], w.xl[k]), __ldcg(yl + so + k));
+        zl[so + k] = dd_mul(__ldg(p.slot_w2 + so + k), z);
+        rz = dd_add(rz, dd_mul(__ldcg(rl + so + k), z));
+    }
+    rz = dd_warp_sum(rz);
+    if ((threadIdx.x & 31) == 0) {
+        p.part_rz[s] = dd_dbl(rz);
+        p.zp[s] = dd_dbl(__ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]));
+    }
+    __syncwarp();
+}
+
+// convergence decision, direction update and operator apply (pairs)
+__device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+    const int b = p.sub_inst[s];
+    if (inst_done(p, b)) return;
+    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
+    const int l = threadIdx.x & 31;
+    if (cache.b != b) {
+        cache.b = b;
+        cache.v0 = range_sum(p.part_rr, s0, s1);
+        cache.v1 = range_sum(p.part_rz, s0, s1);
+    }
+    const double rr = cache.v0, rz = cache.v1;
+    const bool owner = (s == s0);
+    const int64_t hb = (int64_t)b * (p.maxit + 1);
+    double r0, floor_, rho0;
+    if (k == 0) {
+        const double a1 = range_sum(p.part_a1, s0, s1);
+        const double a2 = range_sum(p.part_a2, s0, s1);
+        r0 = sqrt(rr);
+        floor_ = 1e-14 * (sqrt(a1) + sqrt(a2));
+        rho0 = rz;
+    } else {
+        r0 = __ldcg(&p.st[b].r0);
+        floor_ = __ldcg(&p.st[b].floor);
+        rho0 = __ldcg(&p.st[b].rho0);
+    }
+    const double nr = sqrt(rr);
+    const double relres = (k == 0) ? 1.0 : nr / r0;
+    int status = -100;
+    if (k == 0) {
+        if (nr <= floor_ || rz <= 0.0) status = BDDC_OK;
+        else if (!(rz == rz)) status = BDDC_E_BREAKDOWN;
+    } else {
+        if (relres <= p.tol || nr <= floor_ || rz <= kRhoFluxConverged * rho0) status = BDDC_OK;
+        else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
+        else if (k >= p.maxit) status = BDDC_E_NOT_CONVERGED;
+    }
+    if (owner) {
+        if (l == 0) {
+            if (k == 0) {
+                p.st[b].r0 = r0;
+                p.st[b].floor = floor_;
+                p.st[b].rho0 = rho0;
+            }
+            p.rho_hist[hb + k] = rz;
+        }
+        if (status != -100 && l == 0) {
+            p.st[b].status = status;
+            p.st[b].iterations = k;
+            p.st[b].relres = relres;
+            __threadfence();
+            p.st[b].done = 1;
+            atomicSub(p.n_active, 1);
+        }
+    }
+    __syncwarp();
+    if (status != -100) return;
+    const double beta = (k == 0) ? 0.0 : rz / __ldcg(p.rho_hist + hb + k - 1);
+    if (owner && l == 0) p.beta_hist[hb + k] = beta;
+    const float2 beta2 = dd_of(beta);
+    const float2* dold = V2((k & 1) ? p.dbuf0 : p.dbuf1);
+    float2* dnew = V2((k & 1) ? p.dbuf1 : p.dbuf0);
+    double* dpold = (k & 1) ? p.dp0 : p.dp1;
+    double* dpnew = (k & 1) ? p.dp1 : p.dp0;
+    const float2* zl = V2(p.zl);
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s];
+    for (int kk = l; kk < ng; kk += 32) {
+        const int pt = p.slot_partner[so + kk];
+        const int gi = p.slot_g[so + kk];
+        float2 z = __ldcg(zl + so + kk);
+        if (pt >= 0) z = dd_add(z, __ldcg(zl + pt));
+        const float2 dn = (k == 0) ? z : dd_add(z, dd_mul(beta2, __ldcg(dold + gi)));
+        if (slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
+        w.xh[kk] = dn.x;
+        w.xl[kk] = dn.y;
+    }
+    const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
+    if (l == 0) dpnew[s] = dpn;
+    const float2 dpn2 = dd_of(dpn);
+    __syncwarp();
+    const float2* S = reinterpret_cast<const float2*>(p.S) + p.off_S[s];
+    float2* ql = V2(p.ql);
+    float2 dq = dd_zero();
+    for (int kk = l; kk < ng; kk += 32) {
+        const float2 q = dd_add(mx_gemv_S(S, ng, w, kk), dd_mul(__ldg(p.slot_dsig2 + so + kk), dpn2));
+        ql[so + kk] = q;
+        dq = dd_add(dq, dd_mul(make_float2(w.xh[kk], w.xl[kk]), q));
+    }
+    dq = dd_warp_sum(dq);
+    if (l == 0) p.part_dq[s] = dd_dbl(dq);
+    __syncwarp();
+}
+
+__device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+    const int b = p.sub_inst[s];
+    if (inst_done(p, b)) return;
+    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
+    const int64_t hb = (int64_t)b * (p.maxit + 1);
+    const int l = threadIdx.x & 31;
+    if (cache.b != b) {
+        cache.b = b;
+        cache.v0 = range_sum(p.part_dq, s0, s1);
+    }
+    const double dq = cache.v0;
+    const bool owner = (s == s0);
+    if (!(dq > 0.0)) {
+        if (owner && l == 0) {
+            p.st[b].status = BDDC_E_BREAKDOWN;
+            p.st[b].iterations = k;
+            p.st[b].relres = -1.0;
+            __threadfence();
+            p.st[b].done = 1;
+            atomicSub(p.n_active, 1);
+        }
+        __syncwarp();
+        return;
+    }
+    const double alpha = __ldcg(p.rho_hist + hb + k) / dq;
+    if (owner && l == 0) p.alpha_hist[hb + k] = alpha;
+    const float2 alpha2 = dd_of(alpha);
+    const float2* rold = V2((k & 1) ? p.rbuf1 : p.rbuf0);
+    float2* rnew = V2((k & 1) ? p.rbuf0 : p.rbuf1);
+    const float2* dcur = V2((k & 1) ? p.dbuf1 : p.dbuf0);
+    const double* dpcur = (k & 1) ? p.dp1 : p.dp0;
+    const float2* ql = V2(p.ql);
+    float2* x = V2(p.x);
+    float2* rl = V2(p.rl);
+    const int ng = p.sub_ng[s];
+    const int64_t so = p.off_slot[s];
+    float2 rr = dd_zero();
+    for (int kk = l; kk < ng; kk += 32) {
+        const int pt = p.slot_partner[so + kk];
+        const int gi = p.slot_g[so + kk];
+        float2 q = __ldcg(ql + so + kk);
+        if (pt >= 0) q = dd_add(q, __ldcg(ql + pt));
+        const float2 rn = dd_sub(__ldcg(rold + gi), dd_mul(alpha2, q));
+        if (slot_owner((int)(so + kk), pt)) {
+            rnew[gi] = rn;
+            x[gi] = dd_add(__ldcg(x + gi), dd_mul(alpha2, __ldcg(dcur + gi)));
+            rr = dd_add(rr, dd_mul(rn, rn));
+        }
+        const float2 wr = dd_mul(__ldg(p.slot_w2 + so + kk), rn);
+        w.xh[kk] = wr.x;
+        w.xl[kk] = wr.y;
+        rl[so + kk] = wr;
+    }
+    rr = dd_warp_sum(rr);
+    if (l == 0) {
+        p.part_rr[s] = dd_dbl(rr);
+        p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
+    }
+    __syncwarp();
+    mx_restrict(p, s, w);
+}
+
+// closing FP64 coarse pressure correction: FP64 restriction of the final
+// residual (stored as pairs), coarse solve, x_p += p_0
+__device__ void mx_final_restrict(const Params& p, int64_t s, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    const int ng = p.sub_ng[s], m = p.sub_m[s];
+    const int64_t so = p.off_slot[s], co = p.off_cslot[s];
+    const int it = __ldcg(&p.st[b].iterations);
+    const float2* r = V2((it & 1) ? p.rbuf1 : p.rbuf0);
+    for (int k = threadIdx.x & 31; k < ng; k += 32)
+        w.x[k] = p.slot_w[so + k] * dd_dbl(__ldcg(r + p.slot_g[so + k]));
+    __syncwarp();
+    const double* P64 = p.P64 + p.off_P[s];
+    float2* rcl = V2(p.rcl);
+    for (int a = threadIdx.x & 31; a < m; a += 32) {
+        double acc = 0.0;
+        for (int k = 0; k < ng; ++k) acc = fma(__ldg(P64 + (int64_t)a * ng + k), w.x[k], acc);
+        rcl[co + a] = dd_of(acc);
+    }
+    __syncwarp();
+}
+
+__device__ void mx_final_pressure(const Params& p, int64_t s) {
+    if ((threadIdx.x & 31) != 0) return;
+    const int b = p.sub_inst[s];
+    const float2* wcb = V2(p.wc) + p.inst_coff[b];
+    p.xp[s] = __ldcg(p.xp + s) + dd_dbl(__ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]));
+}
+
+__device__ void mx_post(const Params& p, int64_t s, WarpSm& w) {
+    const int ng = p.sub_ng[s], ni = p.sub_ni[s], nc = p.sub_nc[s];
+    const int64_t so = p.off_slot[s], cb = p.off_cell[s], ib = p.off_int[s];
+    const int l = threadIdx.x & 31;
+    const float2* x = V2(p.x);
+    for (int k = l; k < ng; k += 32) {
+        const int gi = p.slot_g[so + k];
+        const double u = __ldcg(p.u0 + gi) + dd_dbl(__ldcg(x + gi));
+        if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.flux_out[p.g_fid[gi]] = u;
+        w.xin[k] = u;
+    }
+    for (int r = l; r < nc; r += 32) w.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
+    __syncwarp();
+    const double* G = p.Gpost + p.off_Gpost[s];
+    const int no = ni + nc, nin = ng + nc;
+    const double d = p.sub_d[s];
+    const double xp = __ldcg(p.xp + s);
+    for (int o = l; o < no; o += 32) {
+        double a0 = 0.0, a1 = 0.0;
+        int j = 0;
+        for (; j + 1 < nin; j += 2) {
+            a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
+            a1 = fma(__ldg(G + (int64_t)(j + 1) * no + o), w.xin[j + 1], a1);
+        }
+        if (j < nin) a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
+        const double v = a0 + a1;
+        if (o < ni) p.flux_out[p.int_fid[ib + o]] = v;
+        else p.p_out[p.cell_gid[cb + o - ni]] = d * (xp + v);
+    }
+    __syncwarp();
+}
