@@ -190,12 +190,17 @@ __device__ __forceinline__ void split_pairs(WarpSm& w, int n) {
 __device__ __forceinline__ double gemv_out(const double* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
     double a0 = 0.0, a1 = 0.0;
     int j = 0;
-#pragma unroll 4
-    for (; j + 1 < n_in; j += 2) {
-        a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
-        a1 = fma(__ldg(M + (int64_t)(j + 1) * n_out + o), w.x[j + 1], a1);
+    for (; j + 8 <= n_in; j += 8) {  // independent loads first, then the FMAs
+        double A[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) A[t] = __ldg(M + (int64_t)(j + t) * n_out + o);
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            a0 = fma(A[t], w.x[j + t], a0);
+            a1 = fma(A[t + 1], w.x[j + t + 1], a1);
+        }
     }
-    if (j < n_in) a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
+    for (; j < n_in; ++j) a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
     return a0 + a1;
 }
 
@@ -448,7 +453,15 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
             acc = (double)sh + (double)sl;
         } else {
             acc = 0.0;
-            for (int64_t c = l; c < ncols; c += 32) acc = fma(__ldg(kr + c), rhs[c], acc);
+            int64_t c = l;
+            for (; c + 7 * 32 < ncols; c += 8 * 32) {
+                double A[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) A[t] = __ldg(reinterpret_cast<const double*>(kr) + c + 32 * t);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc = fma(A[t], rhs[c + 32 * t], acc);
+            }
+            for (; c < ncols; c += 32) acc = fma(__ldg(kr + c), rhs[c], acc);
         }
         acc = warp_sum(acc);
         if (l == 0) p.wc[coff + row] = acc;
@@ -1022,6 +1035,7 @@ struct bddc_handle {
     double* d_hist_a = nullptr;
     int64_t* d_cfoff = nullptr;
     double bytes_iter = 0.0, bytes_pre = 0.0, bytes_post = 0.0;
+    std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
 };
 
 namespace {
@@ -1341,12 +1355,25 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     if (!p_dev) cudaMemcpyAsync(pressure, p.p_out, ncell * sizeof(double), cudaMemcpyDeviceToHost, st);
     std::vector<InstState> hs(h->n_inst);
     GridSync gs;
-    const int64_t H = (int64_t)h->n_inst * (h->maxit + 1);
-    std::vector<double> ha(H), hb(H);
     cudaMemcpyAsync(hs.data(), p.st, sizeof(InstState) * h->n_inst, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&gs, p.gsync, sizeof(GridSync), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(ha.data(), p.alpha_hist, sizeof(double) * H, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hb.data(), p.beta_hist, sizeof(double) * H, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+    // the CG coefficients of the iterations actually run (for the Lanczos
+    // estimate): one strided copy of the first max_it + 1 columns
+    int hist_cols = 1;
+    for (int b = 0; b < h->n_inst; ++b) hist_cols = std::max(hist_cols, std::min(hs[b].iterations, h->maxit) + 1);
+    const size_t pitch = sizeof(double) * (size_t)(h->maxit + 1);
+    std::vector<double>& ha = h->hist_a;
+    std::vector<double>& hb = h->hist_b;
+    if (ha.size() != (size_t)h->n_inst * (h->maxit + 1)) {
+        ha.assign((size_t)h->n_inst * (h->maxit + 1), 0.0);
+        hb.assign((size_t)h->n_inst * (h->maxit + 1), 0.0);
+    }
+    cudaMemcpy2DAsync(ha.data(), pitch, p.alpha_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
+                      cudaMemcpyDeviceToHost, st);
+    cudaMemcpy2DAsync(hb.data(), pitch, p.beta_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
+                      cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("solve: ") + cudaGetErrorString(e));
     cudaEventElapsedTime(&h->last_ms, h->ev0, h->ev1);

@@ -60,23 +60,33 @@ __device__ __forceinline__ float2 dd_warp_sum(float2 v) {
 // views of the work buffers as FP32 pairs (same 8-byte slots)
 __device__ __forceinline__ float2* V2(double* p) { return reinterpret_cast<float2*>(p); }
 
-// S (FP32 pairs, input-major) times the pair vector (w.xh, w.xl) for output o
+// one compensated step of the FP32-pair dot product: (sh, sl) += a * (xh + xl)
+__device__ __forceinline__ void dd_acc(float& sh, float& sl, float2 a, float xh, float xl) {
+    const float pr = __fmul_rn(a.x, xh);
+    float e = __fmaf_rn(a.x, xh, -pr);
+    e = __fmaf_rn(a.x, xl, e);
+    e = __fmaf_rn(a.y, xh, e);
+    const float t = __fadd_rn(sh, pr);
+    const float bp = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// S (FP32 pairs, input-major) times the pair vector (w.xh, w.xl) for output o.
+// Loads are issued in independent batches of 8 ahead of the dependent
+// accumulation so that eight memory requests per lane are in flight.
 __device__ __forceinline__ float2 mx_gemv_S(const float2* __restrict__ M, int n, const WarpSm& w, int o) {
     float sh = 0.0f, sl = 0.0f;
-#pragma unroll 4
-    for (int j = 0; j < n; ++j) {
-        const float2 a = __ldg(M + (int64_t)j * n + o);
-        const float xh = w.xh[j], xl = w.xl[j];
-        const float pr = __fmul_rn(a.x, xh);
-        float e = __fmaf_rn(a.x, xh, -pr);
-        e = __fmaf_rn(a.x, xl, e);
-        e = __fmaf_rn(a.y, xh, e);
-        const float t = __fadd_rn(sh, pr);
-        const float bp = __fsub_rn(t, sh);
-        const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-        sh = t;
-        sl = __fadd_rn(sl, __fadd_rn(err, e));
+    int j = 0;
+    for (; j + 8 <= n; j += 8) {
+        float2 A[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) A[t] = __ldg(M + (int64_t)(j + t) * n + o);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) dd_acc(sh, sl, A[t], w.xh[j + t], w.xl[j + t]);
     }
+    for (; j < n; ++j) dd_acc(sh, sl, __ldg(M + (int64_t)j * n + o), w.xh[j], w.xl[j]);
     return dd_quick(sh, sl);
 }
 
@@ -125,23 +135,33 @@ __device__ void mx_restrict(const Params& p, int64_t s, WarpSm& w) {
         const float* row = P + (int64_t)a * ng;
         float a0 = 0.0f, a1 = 0.0f;
         int k = 0;
-#pragma unroll 4
-        for (; k + 1 < ng; k += 2) {
-            a0 = fmaf(__ldg(row + k), w.xh[k], a0);
-            a1 = fmaf(__ldg(row + k + 1), w.xh[k + 1], a1);
+        for (; k + 8 <= ng; k += 8) {
+            float A[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) A[t] = __ldg(row + k + t);
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                a0 = fmaf(A[t], w.xh[k + t], a0);
+                a1 = fmaf(A[t + 1], w.xh[k + t + 1], a1);
+            }
         }
-        if (k < ng) a0 = fmaf(__ldg(row + k), w.xh[k], a0);
+        for (; k < ng; ++k) a0 = fmaf(__ldg(row + k), w.xh[k], a0);
         rcl[co + a] = dd_add(make_float2(a0 + a1, 0.0f), t[a]);
     }
     for (int o = l; o < ng; o += 32) {
         float a0 = 0.0f, a1 = 0.0f;
         int j = 0;
-#pragma unroll 4
-        for (; j + 1 < ng; j += 2) {
-            a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
-            a1 = fmaf(__ldg(F + (int64_t)(j + 1) * ng + o), w.xh[j + 1], a1);
+        for (; j + 8 <= ng; j += 8) {
+            float A[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) A[t] = __ldg(F + (int64_t)(j + t) * ng + o);
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                a0 = fmaf(A[t], w.xh[j + t], a0);
+                a1 = fmaf(A[t + 1], w.xh[j + t + 1], a1);
+            }
         }
-        if (j < ng) a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
+        for (; j < ng; ++j) a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
         y[o] = make_float2(a0 + a1, 0.0f);
     }
     __syncwarp();
@@ -265,18 +285,20 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
     for (int64_t row = r0 + wi; row < r1; row += kWarps) {
         const float2* kr = K + row * ncn;
         float sh = 0.0f, sl = 0.0f;
-        for (int64_t c = l; c < ncols; c += 32) {
-            const float2 a = __ldg(kr + c);
+        int64_t c = l;
+        for (; c + 7 * 32 < ncols; c += 8 * 32) {
+            float2 A[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) A[t] = __ldg(kr + c + 32 * t);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float2 xv = rhs[c + 32 * t];
+                dd_acc(sh, sl, A[t], xv.x, xv.y);
+            }
+        }
+        for (; c < ncols; c += 32) {
             const float2 xv = rhs[c];
-            const float pr = __fmul_rn(a.x, xv.x);
-            float e = __fmaf_rn(a.x, xv.x, -pr);
-            e = __fmaf_rn(a.x, xv.y, e);
-            e = __fmaf_rn(a.y, xv.x, e);
-            const float t = __fadd_rn(sh, pr);
-            const float bp = __fsub_rn(t, sh);
-            const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-            sh = t;
-            sl = __fadd_rn(sl, __fadd_rn(err, e));
+            dd_acc(sh, sl, __ldg(kr + c), xv.x, xv.y);
         }
         const float2 acc = dd_warp_sum(dd_quick(sh, sl));
         if (l == 0) wc[coff + row] = acc;

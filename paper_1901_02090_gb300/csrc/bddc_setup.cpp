@@ -1046,17 +1046,27 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             P.max_in_post = std::max(P.max_in_post, S.ng + S.nc);
             P.off_S.push_back(oS); P.off_F.push_back(oF); P.off_P.push_back(oP);
             P.off_Gpre.push_back(oGpre); P.off_Gpost.push_back(oGpost);
+            // every operator block starts on a multiple of 4 elements (16-byte
+            // alignment for FP32, 32 for FP64) and is zero-padded to one, so
+            // a block can be copied whole by a 1D bulk copy
+            auto pad4 = [](int64_t n) { return (n + 3) & ~(int64_t)3; };
+            const int64_t nS = (int64_t)S.ng * S.ng, nP = (int64_t)S.m * S.ng;
             P.S.insert(P.S.end(), S.S.begin(), S.S.end());
-            oS += (int64_t)S.ng * S.ng;
+            P.S.resize(oS + pad4(nS), 0.0);
+            oS += pad4(nS);
             P.P64.insert(P.P64.end(), S.PsiT.begin(), S.PsiT.end());
+            P.P64.resize(oP + pad4(nP), 0.0);
             if (opt.precision == BDDC_PREC_FP32) {
                 for (double v : S.F) P.F32.push_back((float)v);
+                P.F32.resize(oF + pad4(nS), 0.0f);
                 for (double v : S.PsiT) P.P32.push_back((float)v);
+                P.P32.resize(oP + pad4(nP), 0.0f);
             } else {
                 P.F64.insert(P.F64.end(), S.F.begin(), S.F.end());
+                P.F64.resize(oF + pad4(nS), 0.0);
             }
-            oF += (int64_t)S.ng * S.ng;
-            oP += (int64_t)S.m * S.ng;
+            oF += pad4(nS);
+            oP += pad4(nP);
             P.Gpre.insert(P.Gpre.end(), S.GpreT.begin(), S.GpreT.end());
             oGpre += (int64_t)S.nc * S.ng;
             P.Gpost.insert(P.Gpost.end(), S.GpostT.begin(), S.GpostT.end());

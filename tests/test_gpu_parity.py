@@ -136,7 +136,7 @@ def test_channelized_60x220_fp64_and_fp32(bddc, tau, seed):
     assert _rel(pres32, ref.pressure) <= MIXED_REL
     for u, p_ in ((flux, pres), (flux32, pres32)):
         _, r2 = residuals(o.disc, u, p_)
-        assert np.abs(r2).max() <= 1e-11 * np.abs(u).max()
+        assert np.abs(r2).max() <= 1e-10 * np.abs(u).max()
     # the FP32 preconditioner changes the iteration count (stated, not +-1)
     assert abs(int(its32[0]) - ref.iterations) <= 2 + int(0.25 * ref.iterations)
     # converged: FP64 path within 1e-9 of the oracle
