@@ -7,11 +7,15 @@
 //           reduced right-hand side f* of eqs. (corr-reduced-1/2);
 //   Step 3  CG on the pairs (w_hat, p_0) with the BDDC preconditioner of
 //           Algorithm 2; per iteration four phases:
-//             DIROP   d = z + beta d, q = S d + B_0^T d_p       (rows a1, a2)
-//             UPDATE  x += alpha d, r -= alpha q, restrict r,
-//                     subdomain correction F r, Psi^T r          (a2, a3, a4, a6)
-//             COARSE  coarse solve                               (a5)
-//             PROLONG z = E (Psi w_c + F r), (r, z)             (a7, a8)
+//             DIROP   d = z + beta d, q = S d + B_0^T d_p, (d, q) -> alpha
+//             UPDATE  x += alpha d, r -= alpha q, (r, r), weighted
+//                     restriction, subdomain correction F r, Psi^T r
+//             COARSE  coarse solve
+//             PROLONG z = E (Psi w_c + F r), (r, z) -> convergence test
+//                     and beta of the next iteration
+//           The scalar step of each instance (alpha, the test, beta) is
+//           taken once, by the warp that completes the instance's partial
+//           inner products.
 //   post    interiors and pressures from the final interface flux.
 // The iterations, the inner products and the coarse solve are FP64; the
 // subdomain-correction operator F and the coarse basis Psi are FP64 or FP32.
@@ -36,6 +40,8 @@
 #include "dense.hpp"
 
 namespace bddc {
+
+#include "bddc_cache.cuh"
 
 // ---- small device helpers --------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -68,6 +74,134 @@ __device__ __forceinline__ double range_sum(const double* part, int64_t s0, int6
     double v = 0.0;
     for (int64_t s = s0 + (threadIdx.x & 31); s < s1; s += 32) v += __ldcg(part + s);
     return warp_sum(v);
+}
+
+// ---- per-instance CG scalars ----------------------------------------------------
+// Each subdomain warp stores its partial of an inner product and counts its
+// arrival with an acquire-release atomic.  The warp whose arrival completes
+// the instance sums the instance's partials in a fixed order (range_sum) and
+// takes the instance's scalar step of CG once: at the end of PROLONG the
+// convergence test of iteration k and its beta (from rr = (r, r) of the last
+// residual update and rz = (r, z)), at the end of DIROP alpha = rho / (d, q).
+// The warps of the next phase read the published values instead of each
+// re-summing the partials and repeating the FP64 arithmetic.  The completing
+// warp resets the count for the next use (after the next grid barrier).
+enum : int { kCtrRR = 0, kCtrRZ = 1, kCtrDQ = 2, kCounters = 3 };
+enum : int { kTotRR = 0, kTotRZ = 1, kTotDQ = 2, kTotA1 = 3, kTotA2 = 4, kTotals = 5 };
+constexpr double kRhoFluxConverged = 1e-24;
+
+__device__ __forceinline__ int arrive_acq_rel(int* cnt) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
+    return old;
+}
+
+// convergence test of iteration k (Sec. 6: relative residual, with the
+// rounding floor and the converged-flux test of (r, z)); beta_k on
+// continuation, the final bookkeeping otherwise.  Whole warp.
+__device__ void cg_decide(const Params& p, int b, int k, double rz, bool fp64_correction) {
+    const int l = threadIdx.x & 31;
+    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
+    const double* tot = p.inst_tot + (int64_t)b * kTotals;
+    const int64_t hb = (int64_t)b * (p.maxit + 1);
+    const double rr = __ldcg(tot + kTotRR);
+    double r0, floor_, rho0;
+    if (k == 0) {
+        r0 = sqrt(rr);
+        floor_ = 1e-14 * (sqrt(__ldcg(tot + kTotA1)) + sqrt(__ldcg(tot + kTotA2)));
+        rho0 = rz;
+    } else {
+        r0 = __ldcg(&p.st[b].r0);
+        floor_ = __ldcg(&p.st[b].floor);
+        rho0 = __ldcg(&p.st[b].rho0);
+    }
+    const double nr = sqrt(rr);
+    const double relres = (k == 0) ? 1.0 : nr / r0;
+    int status = -100;  // not done
+    if (k == 0) {
+        // M is positive semi-definite: (r, z) <= 0 at the start is a rounded
+        // zero, i.e. r lies in range(B_0^T) and the flux is already exact
+        if (nr <= floor_ || rz <= 0.0) status = BDDC_OK;
+        else if (!(rz == rz)) status = BDDC_E_BREAKDOWN;
+    } else {
+        if (relres <= p.tol || nr <= floor_ || rz <= kRhoFluxConverged * rho0) status = BDDC_OK;
+        else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
+        else if (k >= p.maxit) status = BDDC_E_NOT_CONVERGED;
+    }
+    if (l == 0) {
+        if (k == 0) {
+            p.st[b].r0 = r0;
+            p.st[b].floor = floor_;
+            p.st[b].rho0 = rho0;
+        }
+        p.rho_hist[hb + k] = rz;
+        if (status == -100) p.beta_hist[hb + k] = (k == 0) ? 0.0 : rz / __ldcg(p.rho_hist + hb + k - 1);
+    }
+    if (status != -100) {
+        // FP64 path: last coarse pressure correction x_p += z_p from the
+        // final residual (the mixed path does it in FP64 after the loop)
+        if (fp64_correction)
+            for (int64_t t = s0 + l; t < s1; t += 32) p.xp[t] = __ldcg(p.xp + t) + __ldcg(p.zp + t);
+        __syncwarp();
+        if (l == 0) {
+            p.st[b].status = status;
+            p.st[b].iterations = k;
+            p.st[b].relres = relres;
+            __threadfence();
+            p.st[b].done = 1;
+            atomicSub(p.n_active, 1);
+        }
+    }
+    __syncwarp();
+}
+
+// alpha_k = rho_k / (d, q), or breakdown when (d, q) <= 0.  Lane 0.
+__device__ void cg_alpha(const Params& p, int b, int k, double dq) {
+    if ((threadIdx.x & 31) != 0) return;
+    const int64_t hb = (int64_t)b * (p.maxit + 1);
+    if (!(dq > 0.0)) {
+        p.st[b].status = BDDC_E_BREAKDOWN;
+        p.st[b].iterations = k;
+        p.st[b].relres = -1.0;
+        __threadfence();
+        p.st[b].done = 1;
+        atomicSub(p.n_active, 1);
+    } else {
+        p.alpha_hist[hb + k] = __ldcg(p.rho_hist + hb + k) / dq;
+    }
+}
+
+// count this warp's partial of kind ctr (stored by lane 0 before the call);
+// the completing warp publishes the total and takes the scalar step
+__device__ void publish_total(const Params& p, int64_t s, int ctr, int k = 0, bool with_a = false,
+                              bool fp64_correction = false) {
+    const int b = p.sub_inst[s];
+    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
+    int* cnt = p.inst_cnt + (int64_t)b * kCounters + ctr;
+    int last = 0;
+    if ((threadIdx.x & 31) == 0) last = arrive_acq_rel(cnt) == (int)(s1 - s0) - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    const double* part = ctr == kCtrRR ? p.part_rr : (ctr == kCtrRZ ? p.part_rz : p.part_dq);
+    const double v = range_sum(part, s0, s1);
+    double a1 = 0.0, a2 = 0.0;
+    if (with_a) {
+        a1 = range_sum(p.part_a1, s0, s1);
+        a2 = range_sum(p.part_a2, s0, s1);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double* tot = p.inst_tot + (int64_t)b * kTotals;
+        tot[ctr == kCtrRR ? kTotRR : (ctr == kCtrRZ ? kTotRZ : kTotDQ)] = v;
+        if (with_a) {
+            tot[kTotA1] = a1;
+            tot[kTotA2] = a2;
+        }
+        *cnt = 0;
+    }
+    __syncwarp();
+    if (ctr == kCtrRZ) cg_decide(p, b, k, v, fp64_correction);
+    else if (ctr == kCtrDQ) cg_alpha(p, b, k, v);
 }
 
 // grid-wide barrier with a bounded wait; false if any CTA gave up
@@ -185,63 +319,11 @@ __device__ __forceinline__ void split_pairs(WarpSm& w, int n) {
     __syncwarp();
 }
 
-// out = sum_j M[j*n_out + o] * x[j] for one output o of an input-major
-// operator; FP64 or compensated FP32-pair arithmetic
-__device__ __forceinline__ double gemv_out(const double* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
-    double a0 = 0.0, a1 = 0.0;
-    int j = 0;
-    for (; j + 8 <= n_in; j += 8) {  // independent loads first, then the FMAs
-        double A[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) A[t] = __ldg(M + (int64_t)(j + t) * n_out + o);
-#pragma unroll
-        for (int t = 0; t < 8; t += 2) {
-            a0 = fma(A[t], w.x[j + t], a0);
-            a1 = fma(A[t + 1], w.x[j + t + 1], a1);
-        }
-    }
-    for (; j < n_in; ++j) a0 = fma(__ldg(M + (int64_t)j * n_out + o), w.x[j], a0);
-    return a0 + a1;
-}
+#include "bddc_dd.cuh"
+#include "bddc_gemv.cuh"
 
-__device__ __forceinline__ double gemv_out(const float2* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
-    // (sh, sl) accumulates the products of the FP32 pairs (a.x + a.y) and
-    // (xh + xl): the exact error of a.x*xh by FMA, the two cross terms, and a
-    // Knuth two-sum of the high parts; products are rounded explicitly so
-    // that no FMA contraction merges them into the sums
-    float sh = 0.0f, sl = 0.0f;
-#pragma unroll 4
-    for (int j = 0; j < n_in; ++j) {
-        const float2 a = __ldg(M + (int64_t)j * n_out + o);
-        const float xh = w.xh[j], xl = w.xl[j];
-        const float pr = __fmul_rn(a.x, xh);
-        float e = __fmaf_rn(a.x, xh, -pr);
-        e = __fmaf_rn(a.x, xl, e);
-        e = __fmaf_rn(a.y, xh, e);
-        const float t = __fadd_rn(sh, pr);
-        const float bp = __fsub_rn(t, sh);
-        const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-        sh = t;
-        sl = __fadd_rn(sl, __fadd_rn(err, e));
-    }
-    return (double)sh + (double)sl;
-}
-
-// FP32 operator on the FP32 (hi) input
-__device__ __forceinline__ double gemv_out_f(const float* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
-    float a0 = 0.0f, a1 = 0.0f;
-    int j = 0;
-#pragma unroll 4
-    for (; j + 1 < n_in; j += 2) {
-        a0 = fmaf(__ldg(M + (int64_t)j * n_out + o), w.xh[j], a0);
-        a1 = fmaf(__ldg(M + (int64_t)(j + 1) * n_out + o), w.xh[j + 1], a1);
-    }
-    if (j < n_in) a0 = fmaf(__ldg(M + (int64_t)j * n_out + o), w.xh[j], a0);
-    return (double)(a0 + a1);
-}
-__device__ __forceinline__ double gemv_out_f(const double* __restrict__ M, int n_out, int n_in, const WarpSm& w, int o) {
-    return gemv_out(M, n_out, n_in, w, o);
-}
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float2 v) { return dd_dbl(v); }
 
 // restriction rc_a = sum_k P[a*ng + k] x[k]: lane per row a, walking its
 // contiguous row (consecutive loads of one lane share cache lines); all
@@ -358,13 +440,13 @@ __device__ void restrict_apply(const Params& p, int64_t s, WarpSm& w) {
         split_hi(w, ng);
         restrict_rows(P, m, ng, w, p.rcl + co, w.tsum);  // tsum is 0 on adaptive rows
         __syncwarp();
-        for (int k = threadIdx.x & 31; k < ng; k += 32) w.xin[k] = gemv_out_f(F, ng, ng, w, k);
+        gemv_warp(F, ng, w, [&](int k, double v) { w.xin[k] = v; });
         __syncwarp();
         face_sums(p, s, w.xin, w.tsum);
         remove_face_flux(p, s, w.xin, w.tsum);
         for (int k = threadIdx.x & 31; k < ng; k += 32) p.yl[so + k] = w.xin[k];
     } else {
-        for (int k = threadIdx.x & 31; k < ng; k += 32) p.yl[so + k] = gemv_out_f(F, ng, ng, w, k);
+        gemv_warp(F, ng, w, [&](int k, double v) { p.yl[so + k] = v; });
         restrict_rows(P, m, ng, w, p.rcl + co);
     }
     __syncwarp();
@@ -428,6 +510,7 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
         staged = b;
     }
     const K_t* K = reinterpret_cast<const K_t*>(p.Kinv) + p.inst_kinv_off[b];
+    const uint64_t pol = l2_stream_policy();
     const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t r0 = p.cunit_row0[u];
     const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
@@ -437,7 +520,7 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
         if constexpr (PR::kMixed) {
             float sh = 0.0f, sl = 0.0f;
             for (int64_t c = l; c < ncols; c += 32) {
-                const float2 a = __ldg(kr + c);
+                const float2 a = ld_hint(kr + c, pol);
                 const float2 xv = rhs2[c];
                 const float xh = xv.x, xl = xv.y;
                 const float pr = __fmul_rn(a.x, xh);
@@ -457,11 +540,11 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
             for (; c + 7 * 32 < ncols; c += 8 * 32) {
                 double A[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) A[t] = __ldg(reinterpret_cast<const double*>(kr) + c + 32 * t);
+                for (int t = 0; t < 8; ++t) A[t] = ld_hint(reinterpret_cast<const double*>(kr) + c + 32 * t, pol);
 #pragma unroll
                 for (int t = 0; t < 8; ++t) acc = fma(A[t], rhs[c + 32 * t], acc);
             }
-            for (; c < ncols; c += 32) acc = fma(__ldg(kr + c), rhs[c], acc);
+            for (; c < ncols; c += 32) acc = fma(ld_hint(reinterpret_cast<const double*>(kr) + c, pol), rhs[c], acc);
         }
         acc = warp_sum(acc);
         if (l == 0) p.wc[coff + row] = acc;
@@ -504,11 +587,11 @@ __device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
     if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     const double* G = p.Gpre + p.off_Gpre[s];
-    for (int k = l; k < ng; k += 32) {
-        double acc = gemv_out(S, ng, ng, w, k);
+    gemv_warp(S, ng, w, [&](int k, typename GAcc<S_t>::value_type y) {
+        double acc = to_double(y);
         for (int r = 0; r < nc; ++r) acc = fma(__ldg(G + (int64_t)r * ng + k), w.xin[r], acc);
         p.ql[so + k] = acc;
-    }
+    });
     __syncwarp();
 }
 
@@ -548,11 +631,12 @@ __device__ void ph_fstar(const Params& p, int64_t s, WarpSm& w) {
         p.dp1[s] = 0.0;
     }
     __syncwarp();
+    publish_total(p, s, kCtrRR, true);
     restrict_apply<PR>(p, s, w);
 }
 
 template <class PR>
-__device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
     using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
@@ -581,86 +665,17 @@ __device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w) {
         p.zp[s] = __ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]);
     }
     __syncwarp();
+    publish_total(p, s, kCtrRZ, k_next, false, !PR::kMixed);
 }
 
-constexpr double kRhoFluxConverged = 1e-24;
-
-// per-warp cache of an instance's reduced scalars within one phase
-struct InstCache {
-    int b = -1;
-    double v0 = 0.0, v1 = 0.0;
-};
-
-// convergence decision, direction update and operator apply
+// direction update d = z + beta d and operator apply q = S d + B_0^T d_p
 template <class PR>
-__device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+__device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     using S_t = typename PR::S_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
-    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
     const int l = threadIdx.x & 31;
-    if (cache.b != b) {
-        cache.b = b;
-        cache.v0 = range_sum(p.part_rr, s0, s1);
-        cache.v1 = range_sum(p.part_rz, s0, s1);
-    }
-    const double rr = cache.v0, rz = cache.v1;
-    const bool owner = (s == s0);
-    const int64_t hb = (int64_t)b * (p.maxit + 1);
-    double r0, floor_, rho0;
-    if (k == 0) {
-        const double a1 = range_sum(p.part_a1, s0, s1);
-        const double a2 = range_sum(p.part_a2, s0, s1);
-        r0 = sqrt(rr);
-        floor_ = 1e-14 * (sqrt(a1) + sqrt(a2));
-        rho0 = rz;
-    } else {
-        r0 = __ldcg(&p.st[b].r0);
-        floor_ = __ldcg(&p.st[b].floor);
-        rho0 = __ldcg(&p.st[b].rho0);
-    }
-    const double nr = sqrt(rr);
-    const double relres = (k == 0) ? 1.0 : nr / r0;
-    int status = -100;  // not done
-    if (k == 0) {
-        // M is positive semi-definite: (r, z) <= 0 at the start is a rounded
-        // zero, i.e. r lies in range(B_0^T) and the flux is already exact
-        if (nr <= floor_ || rz <= 0.0) status = BDDC_OK;
-        else if (!(rz == rz)) status = BDDC_E_BREAKDOWN;
-    } else {
-        if (relres <= p.tol || nr <= floor_ || rz <= kRhoFluxConverged * rho0) status = BDDC_OK;
-        else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
-        else if (k >= p.maxit) status = BDDC_E_NOT_CONVERGED;
-    }
-    if (owner) {
-        if (l == 0) {
-            if (k == 0) {
-                p.st[b].r0 = r0;
-                p.st[b].floor = floor_;
-                p.st[b].rho0 = rho0;
-            }
-            p.rho_hist[hb + k] = rz;
-        }
-        if (status != -100) {
-            // FP64 path: last coarse pressure correction x_p += z_p from the
-            // final residual (the mixed path does it in FP64 after the loop)
-            if constexpr (!PR::kMixed)
-                for (int64_t t = s0 + l; t < s1; t += 32) p.xp[t] = __ldcg(p.xp + t) + __ldcg(p.zp + t);
-            __syncwarp();
-            if (l == 0) {
-                p.st[b].status = status;
-                p.st[b].iterations = k;
-                p.st[b].relres = relres;
-                __threadfence();
-                p.st[b].done = 1;
-                atomicSub(p.n_active, 1);
-            }
-        }
-    }
-    __syncwarp();
-    if (status != -100) return;
-    const double beta = (k == 0) ? 0.0 : rz / __ldcg(p.rho_hist + hb + k - 1);
-    if (owner && l == 0) p.beta_hist[hb + k] = beta;
+    const double beta = __ldcg(p.beta_hist + (int64_t)b * (p.maxit + 1) + k);
     double* dold = (k & 1) ? p.dbuf0 : p.dbuf1;
     double* dnew = (k & 1) ? p.dbuf1 : p.dbuf0;
     double* dpold = (k & 1) ? p.dp0 : p.dp1;
@@ -681,43 +696,23 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache
     if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     double dq = 0.0;
-    for (int kk = l; kk < ng; kk += 32) {
-        const double q = gemv_out(S, ng, ng, w, kk) + p.slot_dsig[so + kk] * dpn;
+    gemv_warp(S, ng, w, [&](int kk, typename GAcc<S_t>::value_type y) {
+        const double q = to_double(y) + p.slot_dsig[so + kk] * dpn;
         p.ql[so + kk] = q;
         dq += w.x[kk] * q;
-    }
+    });
     dq = warp_sum(dq);
     if (l == 0) p.part_dq[s] = dq;
     __syncwarp();
+    publish_total(p, s, kCtrDQ, k);
 }
 
 template <class PR>
-__device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+__device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
-    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
-    const int64_t hb = (int64_t)b * (p.maxit + 1);
     const int l = threadIdx.x & 31;
-    if (cache.b != b) {
-        cache.b = b;
-        cache.v0 = range_sum(p.part_dq, s0, s1);
-    }
-    const double dq = cache.v0;
-    const bool owner = (s == s0);
-    if (!(dq > 0.0)) {
-        if (owner && l == 0) {
-            p.st[b].status = BDDC_E_BREAKDOWN;
-            p.st[b].iterations = k;
-            p.st[b].relres = -1.0;
-            __threadfence();
-            p.st[b].done = 1;
-            atomicSub(p.n_active, 1);
-        }
-        __syncwarp();
-        return;
-    }
-    const double alpha = __ldcg(p.rho_hist + hb + k) / dq;
-    if (owner && l == 0) p.alpha_hist[hb + k] = alpha;
+    const double alpha = __ldcg(p.alpha_hist + (int64_t)b * (p.maxit + 1) + k);
     const double* rold = (k & 1) ? p.rbuf1 : p.rbuf0;
     double* rnew = (k & 1) ? p.rbuf0 : p.rbuf1;
     const double* dcur = (k & 1) ? p.dbuf1 : p.dbuf0;
@@ -745,6 +740,7 @@ __device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w, InstCach
         p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
     }
     __syncwarp();
+    publish_total(p, s, kCtrRR);
     restrict_apply<PR>(p, s, w);
 }
 
@@ -850,33 +846,32 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     if (!phase_end(p, 5, nts)) return;
     coarse_phase(false);
     if (!phase_end(p, 6, nts)) return;
+    // each PROLONG ends with the convergence test of the next iteration
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_prolong(p, s, w);
-        else ph_prolong<PR>(p, s, w);
+        if constexpr (MX) mx_prolong(p, s, w, 0);
+        else ph_prolong<PR>(p, s, w, 0);
     }
     if (!phase_end(p, 7, nts)) return;
     for (int k = 0;; ++k) {
-        InstCache cache;
+        if (__ldcg(p.n_active) <= 0) break;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_dirop(p, s, k, w, cache);
-            else ph_dirop<PR>(p, s, k, w, cache);
+            if constexpr (MX) mx_dirop(p, s, k, w);
+            else ph_dirop<PR>(p, s, k, w);
         }
         if (!phase_end(p, 8, nts)) return;
-        if (__ldcg(p.n_active) <= 0) break;
-        cache = InstCache();
         for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_update(p, s, k, w, cache);
-            else ph_update<PR>(p, s, k, w, cache);
+            if constexpr (MX) mx_update(p, s, k, w);
+            else ph_update<PR>(p, s, k, w);
         }
         if (!phase_end(p, 9, nts)) return;
         coarse_phase(false);
         if (!phase_end(p, 6, nts)) return;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_prolong(p, s, w);
-            else ph_prolong<PR>(p, s, w);
+            if constexpr (MX) mx_prolong(p, s, w, k + 1);
+            else ph_prolong<PR>(p, s, w, k + 1);
         }
         if (!phase_end(p, 7, nts)) return;
     }
@@ -919,8 +914,9 @@ __global__ void __launch_bounds__(kThreads) k_operator_local(Params p, const dou
         if constexpr (PR::kMixed) split_pairs(w, ng);
         const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
         const double pv = p0[s];
-        for (int k = threadIdx.x & 31; k < ng; k += 32)
-            p.ql[so + k] = gemv_out(S, ng, ng, w, k) + p.slot_dsig[so + k] * pv;
+        gemv_warp(S, ng, w, [&](int k, typename GAcc<S_t>::value_type y) {
+            p.ql[so + k] = to_double(y) + p.slot_dsig[so + k] * pv;
+        });
         __syncwarp();
     }
 }
@@ -1235,6 +1231,7 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     AL(rcl, CL); AL(wc, P.n_coarse_vec);
     AL(xp, NS); AL(dp0, NS); AL(dp1, NS); AL(zp, NS); AL(prhs, NS);
     AL(part_dq, NS); AL(part_rr, NS); AL(part_rz, NS); AL(part_a1, NS); AL(part_a2, NS);
+    AL(inst_cnt, (size_t)n_instances * kCounters); AL(inst_tot, (size_t)n_instances * kTotals);
     AL(st, n_instances); AL(alpha_hist, H); AL(beta_hist, H); AL(rho_hist, H);
     AL(n_active, 1); AL(gsync, 1);
     p.tstamp_cap = 16 + 4 * (opt.maxit + 2);
@@ -1341,6 +1338,7 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     if (rc) return set_err(h, rc, "staging buffers");
     cudaMemsetAsync(p.flux_out, 0, nface * sizeof(double), st);
     cudaMemsetAsync(p.st, 0, sizeof(InstState) * h->n_inst, st);
+    cudaMemsetAsync(p.inst_cnt, 0, sizeof(int) * kCounters * (size_t)h->n_inst, st);
     cudaMemsetAsync(p.gsync, 0, sizeof(GridSync), st);
     cudaMemsetAsync(p.tstamp, 0, 2 * sizeof(long long) * (size_t)p.tstamp_cap, st);
     cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);

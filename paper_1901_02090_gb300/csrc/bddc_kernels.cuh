@@ -86,6 +86,8 @@ struct Params {
     double* wc;                                                // coarse vectors
     double *xp, *dp0, *dp1, *zp, *prhs;                        // per subdomain
     double *part_dq, *part_rr, *part_rz, *part_a1, *part_a2;   // per subdomain partials
+    int* inst_cnt;      // per instance and partial kind: arrivals of subdomain partials
+    double* inst_tot;   // per instance: totals of the partials (rr, rz, dq, a1, a2)
     InstState* st;
     double *alpha_hist, *beta_hist, *rho_hist;                 // n_inst x (maxit + 1)
     int* n_active;

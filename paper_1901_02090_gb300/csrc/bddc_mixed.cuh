@@ -13,83 +13,6 @@
 // coarse inverse are FP32 pairs.
 #pragma once
 
-// ---- double-float arithmetic (FP32 pairs) -------------------------------------------
-// All operations use explicitly rounded intrinsics so that no FMA contraction
-// changes the error-free transformations.
-__device__ __forceinline__ float2 dd_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return make_float2(s, e);
-}
-__device__ __forceinline__ float2 dd_quick(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
-    const float2 s = dd_two_sum(a.x, b.x);
-    return dd_quick(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
-}
-__device__ __forceinline__ float2 dd_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 dd_sub(float2 a, float2 b) { return dd_add(a, dd_neg(b)); }
-__device__ __forceinline__ float2 dd_mul(float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    return dd_quick(p, e);
-}
-// a * sign, sign = +1 or -1 (exact)
-__device__ __forceinline__ float2 dd_sign(float2 a, float sgn) { return sgn > 0.0f ? a : dd_neg(a); }
-__device__ __forceinline__ float2 dd_of(double v) {
-    const float h = __double2float_rn(v);
-    return make_float2(h, __double2float_rn(v - (double)h));
-}
-__device__ __forceinline__ double dd_dbl(float2 a) { return (double)a.x + (double)a.y; }
-__device__ __forceinline__ float2 dd_zero() { return make_float2(0.0f, 0.0f); }
-// xor-butterfly sum: dd_add is commutative, so every lane gets the same bits
-__device__ __forceinline__ float2 dd_warp_sum(float2 v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
-        v = dd_add(v, t);
-    }
-    return v;
-}
-
-// views of the work buffers as FP32 pairs (same 8-byte slots)
-__device__ __forceinline__ float2* V2(double* p) { return reinterpret_cast<float2*>(p); }
-
-// one compensated step of the FP32-pair dot product: (sh, sl) += a * (xh + xl)
-__device__ __forceinline__ void dd_acc(float& sh, float& sl, float2 a, float xh, float xl) {
-    const float pr = __fmul_rn(a.x, xh);
-    float e = __fmaf_rn(a.x, xh, -pr);
-    e = __fmaf_rn(a.x, xl, e);
-    e = __fmaf_rn(a.y, xh, e);
-    const float t = __fadd_rn(sh, pr);
-    const float bp = __fsub_rn(t, sh);
-    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));
-    sh = t;
-    sl = __fadd_rn(sl, __fadd_rn(err, e));
-}
-
-// S (FP32 pairs, input-major) times the pair vector (w.xh, w.xl) for output o.
-// Loads are issued in independent batches of 8 ahead of the dependent
-// accumulation so that eight memory requests per lane are in flight.
-__device__ __forceinline__ float2 mx_gemv_S(const float2* __restrict__ M, int n, const WarpSm& w, int o) {
-    float sh = 0.0f, sl = 0.0f;
-    int j = 0;
-    for (; j + 8 <= n; j += 8) {
-        float2 A[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) A[t] = __ldg(M + (int64_t)(j + t) * n + o);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) dd_acc(sh, sl, A[t], w.xh[j + t], w.xl[j + t]);
-    }
-    for (; j < n; ++j) dd_acc(sh, sl, __ldg(M + (int64_t)j * n + o), w.xh[j], w.xl[j]);
-    return dd_quick(sh, sl);
-}
-
 // face means of a pair vector (vh, vl): t_a = (sum_{k in a} coef_k v_k) / n_a
 // for net-flux rows a, 0 for adaptive rows (lane per row)
 __device__ __forceinline__ void mx_face_means(const Params& p, int64_t s, const float* vh, const float* vl,
@@ -148,22 +71,7 @@ __device__ void mx_restrict(const Params& p, int64_t s, WarpSm& w) {
         for (; k < ng; ++k) a0 = fmaf(__ldg(row + k), w.xh[k], a0);
         rcl[co + a] = dd_add(make_float2(a0 + a1, 0.0f), t[a]);
     }
-    for (int o = l; o < ng; o += 32) {
-        float a0 = 0.0f, a1 = 0.0f;
-        int j = 0;
-        for (; j + 8 <= ng; j += 8) {
-            float A[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) A[t] = __ldg(F + (int64_t)(j + t) * ng + o);
-#pragma unroll
-            for (int t = 0; t < 8; t += 2) {
-                a0 = fmaf(A[t], w.xh[j + t], a0);
-                a1 = fmaf(A[t + 1], w.xh[j + t + 1], a1);
-            }
-        }
-        for (; j < ng; ++j) a0 = fmaf(__ldg(F + (int64_t)j * ng + o), w.xh[j], a0);
-        y[o] = make_float2(a0 + a1, 0.0f);
-    }
+    gemv_warp(F, ng, w, [&](int o, double v) { y[o] = make_float2((float)v, 0.0f); });
     __syncwarp();
     // P_Z on y (face means of y; y's low parts are zero)
     for (int a = l; a < m; a += 32) {
@@ -278,6 +186,7 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
         staged = b;
     }
     const float2* K = reinterpret_cast<const float2*>(p.Kinv) + p.inst_kinv_off[b];
+    const uint64_t pol = l2_stream_policy();
     const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t r0 = p.cunit_row0[u];
     const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
@@ -289,7 +198,7 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
         for (; c + 7 * 32 < ncols; c += 8 * 32) {
             float2 A[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) A[t] = __ldg(kr + c + 32 * t);
+            for (int t = 0; t < 8; ++t) A[t] = ld_hint(kr + c + 32 * t, pol);
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const float2 xv = rhs[c + 32 * t];
@@ -298,7 +207,7 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
         }
         for (; c < ncols; c += 32) {
             const float2 xv = rhs[c];
-            dd_acc(sh, sl, __ldg(kr + c), xv.x, xv.y);
+            dd_acc(sh, sl, ld_hint(kr + c, pol), xv.x, xv.y);
         }
         const float2 acc = dd_warp_sum(dd_quick(sh, sl));
         if (l == 0) wc[coff + row] = acc;
@@ -355,10 +264,11 @@ __device__ void mx_fstar(const Params& p, int64_t s, WarpSm& w) {
         p.dp1[s] = 0.0;
     }
     __syncwarp();
+    publish_total(p, s, kCtrRR, true);
     mx_restrict(p, s, w);
 }
 
-__device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
     const int ng = p.sub_ng[s];
@@ -381,67 +291,15 @@ __device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w) {
         p.zp[s] = dd_dbl(__ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]));
     }
     __syncwarp();
+    publish_total(p, s, kCtrRZ, k_next);
 }
 
-// convergence decision, direction update and operator apply (pairs)
-__device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+// direction update and operator apply (pairs)
+__device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
-    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
     const int l = threadIdx.x & 31;
-    if (cache.b != b) {
-        cache.b = b;
-        cache.v0 = range_sum(p.part_rr, s0, s1);
-        cache.v1 = range_sum(p.part_rz, s0, s1);
-    }
-    const double rr = cache.v0, rz = cache.v1;
-    const bool owner = (s == s0);
-    const int64_t hb = (int64_t)b * (p.maxit + 1);
-    double r0, floor_, rho0;
-    if (k == 0) {
-        const double a1 = range_sum(p.part_a1, s0, s1);
-        const double a2 = range_sum(p.part_a2, s0, s1);
-        r0 = sqrt(rr);
-        floor_ = 1e-14 * (sqrt(a1) + sqrt(a2));
-        rho0 = rz;
-    } else {
-        r0 = __ldcg(&p.st[b].r0);
-        floor_ = __ldcg(&p.st[b].floor);
-        rho0 = __ldcg(&p.st[b].rho0);
-    }
-    const double nr = sqrt(rr);
-    const double relres = (k == 0) ? 1.0 : nr / r0;
-    int status = -100;
-    if (k == 0) {
-        if (nr <= floor_ || rz <= 0.0) status = BDDC_OK;
-        else if (!(rz == rz)) status = BDDC_E_BREAKDOWN;
-    } else {
-        if (relres <= p.tol || nr <= floor_ || rz <= kRhoFluxConverged * rho0) status = BDDC_OK;
-        else if (!(rz > 0.0)) status = BDDC_E_BREAKDOWN;
-        else if (k >= p.maxit) status = BDDC_E_NOT_CONVERGED;
-    }
-    if (owner) {
-        if (l == 0) {
-            if (k == 0) {
-                p.st[b].r0 = r0;
-                p.st[b].floor = floor_;
-                p.st[b].rho0 = rho0;
-            }
-            p.rho_hist[hb + k] = rz;
-        }
-        if (status != -100 && l == 0) {
-            p.st[b].status = status;
-            p.st[b].iterations = k;
-            p.st[b].relres = relres;
-            __threadfence();
-            p.st[b].done = 1;
-            atomicSub(p.n_active, 1);
-        }
-    }
-    __syncwarp();
-    if (status != -100) return;
-    const double beta = (k == 0) ? 0.0 : rz / __ldcg(p.rho_hist + hb + k - 1);
-    if (owner && l == 0) p.beta_hist[hb + k] = beta;
+    const double beta = __ldcg(p.beta_hist + (int64_t)b * (p.maxit + 1) + k);
     const float2 beta2 = dd_of(beta);
     const float2* dold = V2((k & 1) ? p.dbuf0 : p.dbuf1);
     float2* dnew = V2((k & 1) ? p.dbuf1 : p.dbuf0);
@@ -467,42 +325,22 @@ __device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w, InstCache
     const float2* S = reinterpret_cast<const float2*>(p.S) + p.off_S[s];
     float2* ql = V2(p.ql);
     float2 dq = dd_zero();
-    for (int kk = l; kk < ng; kk += 32) {
-        const float2 q = dd_add(mx_gemv_S(S, ng, w, kk), dd_mul(__ldg(p.slot_dsig2 + so + kk), dpn2));
+    gemv_warp(S, ng, w, [&](int kk, float2 y) {
+        const float2 q = dd_add(y, dd_mul(__ldg(p.slot_dsig2 + so + kk), dpn2));
         ql[so + kk] = q;
         dq = dd_add(dq, dd_mul(make_float2(w.xh[kk], w.xl[kk]), q));
-    }
+    });
     dq = dd_warp_sum(dq);
     if (l == 0) p.part_dq[s] = dd_dbl(dq);
     __syncwarp();
+    publish_total(p, s, kCtrDQ, k);
 }
 
-__device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w, InstCache& cache) {
+__device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return;
-    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
-    const int64_t hb = (int64_t)b * (p.maxit + 1);
     const int l = threadIdx.x & 31;
-    if (cache.b != b) {
-        cache.b = b;
-        cache.v0 = range_sum(p.part_dq, s0, s1);
-    }
-    const double dq = cache.v0;
-    const bool owner = (s == s0);
-    if (!(dq > 0.0)) {
-        if (owner && l == 0) {
-            p.st[b].status = BDDC_E_BREAKDOWN;
-            p.st[b].iterations = k;
-            p.st[b].relres = -1.0;
-            __threadfence();
-            p.st[b].done = 1;
-            atomicSub(p.n_active, 1);
-        }
-        __syncwarp();
-        return;
-    }
-    const double alpha = __ldcg(p.rho_hist + hb + k) / dq;
-    if (owner && l == 0) p.alpha_hist[hb + k] = alpha;
+    const double alpha = __ldcg(p.alpha_hist + (int64_t)b * (p.maxit + 1) + k);
     const float2 alpha2 = dd_of(alpha);
     const float2* rold = V2((k & 1) ? p.rbuf1 : p.rbuf0);
     float2* rnew = V2((k & 1) ? p.rbuf0 : p.rbuf1);
@@ -536,6 +374,7 @@ __device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w, InstCach
         p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
     }
     __syncwarp();
+    publish_total(p, s, kCtrRR);
     mx_restrict(p, s, w);
 }
 

@@ -931,6 +931,17 @@ SetupResult coarse(Inst& I) {
 
 }  // namespace
 
+// make an n x n matrix exactly symmetric: both triangles get the mean of the
+// two rounded entries
+static void symmetrize(std::vector<double>& M, int n) {
+    for (int r = 0; r < n; ++r)
+        for (int c = r + 1; c < n; ++c) {
+            const double v = 0.5 * (M[(size_t)r * n + c] + M[(size_t)c * n + r]);
+            M[(size_t)r * n + c] = v;
+            M[(size_t)c * n + r] = v;
+        }
+}
+
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P) {
     const int nthreads = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     std::vector<Inst> I(n_inst);
@@ -1051,6 +1062,11 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             // a block can be copied whole by a 1D bulk copy
             auto pad4 = [](int64_t n) { return (n + 3) & ~(int64_t)3; };
             const int64_t nS = (int64_t)S.ng * S.ng, nP = (int64_t)S.m * S.ng;
+            // S and F are symmetric in exact arithmetic; store them exactly
+            // symmetric (mean of the two rounded triangles) so that one
+            // triangle describes each, as the device keeps it
+            symmetrize(S.S, S.ng);
+            symmetrize(S.F, S.ng);
             P.S.insert(P.S.end(), S.S.begin(), S.S.end());
             P.S.resize(oS + pad4(nS), 0.0);
             oS += pad4(nS);
