@@ -582,14 +582,20 @@ __device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
         if (slot_owner((int)(so + k), pt)) p.u0[p.slot_g[so + k]] = u;
         w.x[k] = u;
     }
-    for (int r = l; r < nc; r += 32) w.xin[r] = p.f_in[p.cell_gid[cb + r]];
+    int nz = 0;
+    for (int r = l; r < nc; r += 32) {
+        const double fv = p.f_in[p.cell_gid[cb + r]];
+        w.xin[r] = fv;
+        nz |= (fv != 0.0);
+    }
+    const int nsrc = __any_sync(0xffffffffu, nz) ? nc : 0;  // f = 0: G_pre f vanishes exactly
     __syncwarp();
     if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     const double* G = p.Gpre + p.off_Gpre[s];
     gemv_warp(S, ng, w, [&](int k, typename GAcc<S_t>::value_type y) {
         double acc = to_double(y);
-        for (int r = 0; r < nc; ++r) acc = fma(__ldg(G + (int64_t)r * ng + k), w.xin[r], acc);
+        for (int r = 0; r < nsrc; ++r) acc = fma(__ldg(G + (int64_t)r * ng + k), w.xin[r], acc);
         p.ql[so + k] = acc;
     });
     __syncwarp();
@@ -775,10 +781,17 @@ __device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
         if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.flux_out[p.g_fid[gi]] = u;
         w.xin[k] = u;
     }
-    for (int r = l; r < nc; r += 32) w.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
+    int nz = 0;
+    for (int r = l; r < nc; r += 32) {
+        const double fv = p.f_in[p.cell_gid[cb + r]];
+        w.xin[ng + r] = fv;
+        nz |= (fv != 0.0);
+    }
+    // a subdomain without sources has f = 0: its f columns contribute exactly nothing
+    const int nin = ng + (__any_sync(0xffffffffu, nz) ? nc : 0);
     __syncwarp();
     const double* G = p.Gpost + p.off_Gpost[s];
-    const int no = ni + nc, nin = ng + nc;
+    const int no = ni + nc;
     const double d = p.sub_d[s];
     const double xp = __ldcg(p.xp + s);
     for (int o = l; o < no; o += 32) {
@@ -1207,6 +1220,7 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
             if (!rc) rc = upload(h, P.P32, &pp);
             if (!rc) rc = upload(h, pairs(P.S), &s2);
             if (!rc) rc = upload(h, pairs(P.Kinv), &k2);
+            if (!rc) rc = upload(h, pairs(P.Gpost), &p.Gpost2);
             p.F = f;
             p.P = pp;
             p.S = s2;
@@ -1285,8 +1299,10 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     for (int64_t s = 0; s < NS; ++s) {
         const double ng = P.sub_ng[s], m = P.sub_m[s], nc = P.sub_nc[s], ni = P.sub_ni[s];
         it_b += 8.0 * ng * ng + fb * ng * ng + 2.0 * fb * m * ng + 8.0 * 18.0 * ng;
-        pre_b += 3.0 * fb * m * ng + 8.0 * ng * ng + 8.0 * nc * ng + fb * ng * ng + 8.0 * 20.0 * ng;
-        post_b += 8.0 * (ng + nc) * (ni + nc) + 8.0 * (ni + 2.0 * nc + 2.0 * ng);
+        // the source columns of G_pre and G_post are not counted: they are
+        // skipped for source-free subdomains
+        pre_b += 3.0 * fb * m * ng + 8.0 * ng * ng + fb * ng * ng + 8.0 * 20.0 * ng;
+        post_b += 8.0 * ng * (ni + nc) + 8.0 * (ni + 2.0 * nc + 2.0 * ng);
     }
     for (int b = 0; b < n_instances; ++b) {
         const double ncn = P.inst_ncn[b], ncf = P.inst_ncf[b];

@@ -79,6 +79,7 @@ struct Params {
     // F and P are double or float; P64 is always FP64
     const void *S, *F, *P, *Kinv;
     const double *P64, *Gpre, *Gpost;
+    const float2* Gpost2;  // mixed path: Gpost as FP32 pairs
     // work vectors
     double *x, *rbuf0, *rbuf1, *dbuf0, *dbuf1, *g, *u0;        // interface
     double *ql, *zl, *yl, *rl, *tl;                            // local slots

@@ -417,21 +417,34 @@ __device__ void mx_post(const Params& p, int64_t s, WarpSm& w) {
         if (slot_owner((int)(so + k), p.slot_partner[so + k])) p.flux_out[p.g_fid[gi]] = u;
         w.xin[k] = u;
     }
-    for (int r = l; r < nc; r += 32) w.xin[ng + r] = p.f_in[p.cell_gid[cb + r]];
+    int nz = 0;
+    for (int r = l; r < nc; r += 32) {
+        const double fv = p.f_in[p.cell_gid[cb + r]];
+        w.xin[ng + r] = fv;
+        nz |= (fv != 0.0);
+    }
+    // a subdomain without sources has f = 0: its f columns contribute exactly nothing
+    const int nin = ng + (__any_sync(0xffffffffu, nz) ? nc : 0);
     __syncwarp();
-    const double* G = p.Gpost + p.off_Gpost[s];
-    const int no = ni + nc, nin = ng + nc;
+    float2* xin2 = V2(w.xin);  // the inputs as FP32 pairs, in place
+    for (int k = l; k < nin; k += 32) xin2[k] = dd_of(w.xin[k]);
+    __syncwarp();
+    const float2* G = p.Gpost2 + p.off_Gpost[s];
+    const int no = ni + nc;
     const double d = p.sub_d[s];
     const double xp = __ldcg(p.xp + s);
     for (int o = l; o < no; o += 32) {
-        double a0 = 0.0, a1 = 0.0;
+        float h = 0.0f, lo = 0.0f;
         int j = 0;
-        for (; j + 1 < nin; j += 2) {
-            a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
-            a1 = fma(__ldg(G + (int64_t)(j + 1) * no + o), w.xin[j + 1], a1);
+        for (; j + 8 <= nin; j += 8) {
+            float2 A[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) A[t] = __ldg(G + (int64_t)(j + t) * no + o);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) dd_acc(h, lo, A[t], xin2[j + t].x, xin2[j + t].y);
         }
-        if (j < nin) a0 = fma(__ldg(G + (int64_t)j * no + o), w.xin[j], a0);
-        const double v = a0 + a1;
+        for (; j < nin; ++j) dd_acc(h, lo, __ldg(G + (int64_t)j * no + o), xin2[j].x, xin2[j].y);
+        const double v = dd_dbl(dd_quick(h, lo));
         if (o < ni) p.flux_out[p.int_fid[ib + o]] = v;
         else p.p_out[p.cell_gid[cb + o - ni]] = d * (xp + v);
     }

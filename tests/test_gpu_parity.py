@@ -146,6 +146,29 @@ def test_channelized_60x220_fp64_and_fp32(bddc, tau, seed):
     assert _rel(pres, ref.pressure) <= CONVERGED_REL
 
 
+@pytest.mark.parametrize("pure_flux", [False, True])
+def test_channelized_60x220_sources_both_precisions(bddc, pure_flux):
+    """Corner wells on the 60 x 220 channelized field (sources in two
+    subdomains, none elsewhere, so both the source and the source-free form
+    of Step 2 and of the post-correction run in one solve): FP64 and FP32-apply
+    paths against the oracle, cellwise conservative."""
+    from oracle.discretization import residuals
+    pb = _wells(make_config("c2", seed=2091), pure_flux=pure_flux)
+    assert np.count_nonzero(pb.f) == 2
+    o = BDDCOracle(pb, tau=10.0)
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, 10.0, precision=bddc.BDDC_PREC_FP64)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    flux32, pres32, its32, st32, _ = gpu_solve(bddc, [pb], 1e-8, 10.0, precision=bddc.BDDC_PREC_FP32)
+    assert _rel(flux32, ref.flux) <= MIXED_REL
+    assert _rel(pres32, ref.pressure) <= MIXED_REL
+    for u, p_ in ((flux, pres), (flux32, pres32)):
+        r1, r2 = residuals(o.disc, u, p_)
+        assert np.abs(r2).max() <= 1e-10 * np.abs(u).max()
+
+
 def test_operator_and_preconditioner_match_oracle(bddc):
     pb = make_config("c1")
     o = BDDCOracle(pb, tau=3.0)
