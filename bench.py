@@ -35,7 +35,7 @@ WORKLOAD = ("2D 60x220 channelized (contrast ~1e7), 6x22 subdomains of 10x10 cel
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64)
@@ -73,10 +73,25 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi takes a while to start: wait for its first sample, then
+        # count only the samples written after the timed region began
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self._lines() == 0 and self.proc.poll() is None:
+            time.sleep(0.02)
+        self.skip = self._lines()
+
+    def _lines(self):
+        self.fh.flush()
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def stop(self):
         if self.proc is None:
@@ -89,7 +104,7 @@ class Clocks:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in list(open(self.path))[getattr(self, "skip", 0):]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -112,6 +127,41 @@ def measured_peak():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bddc_solve_kernel_traffic_c2_batch64.txt")
+
+
+def kernel_source_digest():
+    """sha256 over the solver's CUDA sources: a measured DRAM traffic figure
+    is valid only for the sources it was captured with."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1901_02090_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(batch):
+    """DRAM bytes per launch of the solve kernel from the committed ncu
+    capture of this workload, or None when absent, for another batch, or
+    taken on other kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if "=" in line and not line.lstrip().startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    try:
+        if kv.get("source_sha256") != kernel_source_digest() or int(kv.get("batch", -1)) != batch:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(tau, tol, n_solves=1):
@@ -287,13 +337,14 @@ def main():
         "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
         "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
         "fp64_single": fp64_single,
-        "latency_batched_ms": {"p50": total_ms / K, "p99": max(kms)},
+        "latency_batched_ms": {"p50": float(np.percentile(kms, 50)), "p99": float(np.percentile(kms, 99)),
+                               "per_step_wall": total_ms / K, "note": "kernel time of one batch (CUDA events)"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(8 * (len(f_h) + len(bc_h))),
                 "d2h_bytes_per_step": int(8 * (len(flux_h) + len(pres_h)) + 4 * B)},
         "gpu_launches": K,  # one persistent-kernel launch per step
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "bddc_solve_kernel<float> (persistent Steps 1-3 + post)",
+                     "frac": achieved / peak, "traffic": measured_traffic(B), "peak_kind": peak_kind,
+                     "kernel": "bddc_solve_kernel<PrecMixed> (persistent Steps 1-3 + post)",
                      "kernel_ms_mean": avg_ms, "algorithmic_bytes_per_launch": avg_bytes},
         "clocks": clk,
     }

@@ -98,7 +98,8 @@ typedef struct {
 typedef struct {
     int iterations;        /* CG iterations of Step 3 */
     int status;            /* BDDC_OK, BDDC_E_NOT_CONVERGED or BDDC_E_BREAKDOWN */
-    double kappa;          /* Lanczos estimate from the CG coefficients (Sec. 5) */
+    double kappa;          /* Lanczos estimate from the CG coefficients (Sec. 5); computed on the
+                              first bddc_get_stats call after a solve */
     double relres;         /* final ||r||/||r_0|| of the reduced system */
     double omega_tilde;    /* condition indicator, eq. (indicator); 0 if none */
     int n_subdomains;      /* N */

@@ -1032,7 +1032,10 @@ struct bddc_handle {
     Params prm{};
     std::vector<void*> allocs;
     std::string err;
-    std::vector<bddc_stats> stats;
+    mutable std::vector<bddc_stats> stats;  // kappa filled on demand (bddc_get_stats)
+    mutable bool kappa_stale = false;       // the last solve's kappa is not computed yet
+    InstState* pin_st = nullptr;            // pinned read-back of the per-instance state
+    GridSync* pin_gs = nullptr;
     std::vector<int64_t> inst_cfoff;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     float last_ms = 0.0f;
@@ -1044,7 +1047,7 @@ struct bddc_handle {
     double* d_hist_a = nullptr;
     int64_t* d_cfoff = nullptr;
     double bytes_iter = 0.0, bytes_pre = 0.0, bytes_post = 0.0;
-    std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
+    mutable std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
 };
 
 namespace {
@@ -1117,6 +1120,8 @@ const char* bddc_last_error(const bddc_handle* h) { return h ? h->err.c_str() : 
 void bddc_destroy(bddc_handle* h) {
     if (!h) return;
     for (void* p : h->allocs) cudaFree(p);
+    if (h->pin_st) cudaFreeHost(h->pin_st);
+    if (h->pin_gs) cudaFreeHost(h->pin_gs);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
@@ -1283,6 +1288,11 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     }
     cudaEventCreate(&h->ev0);
     cudaEventCreate(&h->ev1);
+    if (cudaMallocHost((void**)&h->pin_st, sizeof(InstState) * n_instances) != cudaSuccess ||
+        cudaMallocHost((void**)&h->pin_gs, sizeof(GridSync)) != cudaSuccess) {
+        bddc_destroy(h);
+        return BDDC_E_OOM;
+    }
     h->stats.assign(n_instances, bddc_stats{});
     for (int b = 0; b < n_instances; ++b) {
         h->stats[b].omega_tilde = P.inst_omega[b];
@@ -1367,16 +1377,53 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     if (!flux_dev) cudaMemcpyAsync(flux, p.flux_out, nface * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!p_dev) cudaMemcpyAsync(pressure, p.p_out, ncell * sizeof(double), cudaMemcpyDeviceToHost, st);
-    std::vector<InstState> hs(h->n_inst);
-    GridSync gs;
-    cudaMemcpyAsync(hs.data(), p.st, sizeof(InstState) * h->n_inst, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&gs, p.gsync, sizeof(GridSync), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h->pin_st, p.st, sizeof(InstState) * h->n_inst, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h->pin_gs, p.gsync, sizeof(GridSync), cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("solve: ") + cudaGetErrorString(e));
-    // the CG coefficients of the iterations actually run (for the Lanczos
-    // estimate): one strided copy of the first max_it + 1 columns
+    const InstState* hs = h->pin_st;
+    const GridSync& gs = *h->pin_gs;
+    cudaEventElapsedTime(&h->last_ms, h->ev0, h->ev1);
+    if (gs.error) return set_err(h, BDDC_E_TIMEOUT, "grid barrier wait exceeded its limit");
+    int ret = BDDC_OK;
+    double total_it = 0.0;
+    int max_it = 0;
+    std::vector<int> its_h(h->n_inst);
+    for (int b = 0; b < h->n_inst; ++b) {
+        bddc_stats& S = h->stats[b];
+        S.iterations = hs[b].iterations;
+        S.status = hs[b].done ? hs[b].status : BDDC_E_TIMEOUT;
+        S.relres = hs[b].relres;
+        const int m = S.iterations;
+        S.kappa = 0.0;  // computed on demand from the CG coefficients
+        its_h[b] = S.iterations;
+        if (S.status != BDDC_OK && ret == BDDC_OK) ret = S.status;
+        total_it += m;
+        max_it = std::max(max_it, m);
+    }
+    if (iterations) {  // one copy for the whole batch
+        if (is_device_ptr(iterations)) {
+            cudaMemcpyAsync(iterations, its_h.data(), sizeof(int) * its_h.size(), cudaMemcpyHostToDevice, st);
+            cudaStreamSynchronize(st);
+        } else {
+            std::copy(its_h.begin(), its_h.end(), iterations);
+        }
+    }
+    // work of the kernel: every instance runs its own iterations; the
+    // persistent loop streams only active instances' operators
+    h->last_bytes = h->bytes_pre + h->bytes_post + h->bytes_iter * (total_it / std::max(1, h->n_inst));
+    h->kappa_stale = true;
+    if (ret != BDDC_OK) set_err(h, ret, "one or more instances did not converge");
+    return ret;
+}
+
+namespace {
+// Lanczos estimate of the condition number from the CG coefficients of the
+// last solve (Sec. 5): extreme eigenvalues of the tridiagonal matrix built
+// from alpha and beta.  Fetches the used columns of the coefficient history.
+void compute_kappa(const bddc_handle* h) {
     int hist_cols = 1;
-    for (int b = 0; b < h->n_inst; ++b) hist_cols = std::max(hist_cols, std::min(hs[b].iterations, h->maxit) + 1);
+    for (int b = 0; b < h->n_inst; ++b) hist_cols = std::max(hist_cols, std::min(h->stats[b].iterations, h->maxit) + 1);
     const size_t pitch = sizeof(double) * (size_t)(h->maxit + 1);
     std::vector<double>& ha = h->hist_a;
     std::vector<double>& hb = h->hist_b;
@@ -1384,51 +1431,29 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
         ha.assign((size_t)h->n_inst * (h->maxit + 1), 0.0);
         hb.assign((size_t)h->n_inst * (h->maxit + 1), 0.0);
     }
-    cudaMemcpy2DAsync(ha.data(), pitch, p.alpha_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
-                      cudaMemcpyDeviceToHost, st);
-    cudaMemcpy2DAsync(hb.data(), pitch, p.beta_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
-                      cudaMemcpyDeviceToHost, st);
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("solve: ") + cudaGetErrorString(e));
-    cudaEventElapsedTime(&h->last_ms, h->ev0, h->ev1);
-    if (gs.error) return set_err(h, BDDC_E_TIMEOUT, "grid barrier wait exceeded its limit");
-    int ret = BDDC_OK;
-    double total_it = 0.0;
-    int max_it = 0;
+    cudaMemcpy2D(ha.data(), pitch, h->prm.alpha_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
+                 cudaMemcpyDeviceToHost);
+    cudaMemcpy2D(hb.data(), pitch, h->prm.beta_hist, pitch, sizeof(double) * hist_cols, h->n_inst,
+                 cudaMemcpyDeviceToHost);
     for (int b = 0; b < h->n_inst; ++b) {
         bddc_stats& S = h->stats[b];
-        S.iterations = hs[b].iterations;
-        S.status = hs[b].done ? hs[b].status : BDDC_E_TIMEOUT;
-        S.relres = hs[b].relres;
-        // Lanczos estimate from the CG coefficients (Sec. 5)
         const int m = S.iterations;
         S.kappa = 1.0;
-        if (m > 0) {
-            std::vector<double> dd(m), ee(std::max(m - 1, 1));
-            const double* al = &ha[(size_t)b * (h->maxit + 1)];
-            const double* be = &hb[(size_t)b * (h->maxit + 1)];
-            for (int k = 0; k < m; ++k) {
-                dd[k] = 1.0 / al[k] + (k > 0 ? be[k] / al[k - 1] : 0.0);
-                if (k + 1 < m) ee[k] = std::sqrt(be[k + 1]) / al[k];
-            }
-            double lmin, lmax;
-            tridiag_extremes(m, dd.data(), ee.data(), &lmin, &lmax);
-            S.kappa = lmax / lmin;
+        if (m <= 0) continue;
+        std::vector<double> dd(m), ee(std::max(m - 1, 1));
+        const double* al = &ha[(size_t)b * (h->maxit + 1)];
+        const double* be = &hb[(size_t)b * (h->maxit + 1)];
+        for (int k = 0; k < m; ++k) {
+            dd[k] = 1.0 / al[k] + (k > 0 ? be[k] / al[k - 1] : 0.0);
+            if (k + 1 < m) ee[k] = std::sqrt(be[k + 1]) / al[k];
         }
-        if (iterations) {
-            if (is_device_ptr(iterations)) cudaMemcpy(iterations + b, &S.iterations, sizeof(int), cudaMemcpyHostToDevice);
-            else iterations[b] = S.iterations;
-        }
-        if (S.status != BDDC_OK && ret == BDDC_OK) ret = S.status;
-        total_it += m;
-        max_it = std::max(max_it, m);
+        double lmin, lmax;
+        tridiag_extremes(m, dd.data(), ee.data(), &lmin, &lmax);
+        S.kappa = lmax / lmin;
     }
-    // work of the kernel: every instance runs its own iterations; the
-    // persistent loop streams only active instances' operators
-    h->last_bytes = h->bytes_pre + h->bytes_post + h->bytes_iter * (total_it / std::max(1, h->n_inst));
-    if (ret != BDDC_OK) set_err(h, ret, "one or more instances did not converge");
-    return ret;
+    h->kappa_stale = false;
 }
+}  // namespace
 
 int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64_t* count) {
     if (!h || !name) return BDDC_E_INVALID_ARG;
@@ -1476,6 +1501,7 @@ int bddc_debug_phase_times(const bddc_handle* h, int64_t* pairs, int64_t* count)
 
 int bddc_get_stats(const bddc_handle* h, int instance, bddc_stats* out) {
     if (!h || !out || instance < 0 || instance >= h->n_inst) return BDDC_E_INVALID_ARG;
+    if (h->kappa_stale) compute_kappa(h);
     *out = h->stats[instance];
     return BDDC_OK;
 }
