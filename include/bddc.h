@@ -250,6 +250,77 @@ const char* bddc_last_error(const bddc_handle* h);
 const char* bddc_error_string(int code);
 void bddc_destroy(bddc_handle* h);
 
+/* ---- serving: continuous batching of independent solves --------------------
+ * Not a method of the paper: a request loop over the batch solver above, for
+ * a stream of independent problems of any sizes.
+ *
+ * bddc_submit copies a request (host arrays) and returns a ticket at once.
+ * A setup thread takes the requests in arrival order (consecutive requests
+ * with equal tol, at most max_batch), runs their host setup (Algorithm 3 and
+ * the local maps), admits the batch when its device footprint fits the HBM
+ * budget beside the batches already on the device, and uploads it.  A solve
+ * thread runs the admitted batches on the GPU one after another (one launch
+ * of the persistent kernel each).  The host setup and the upload of the next
+ * batch overlap the solve of the current one, and requests that arrive while
+ * a batch is on the GPU join the next batch.  Results are collected by ticket
+ * with bddc_poll (and waited for with bddc_wait).
+ *
+ * The result of a request is bitwise the same as bddc_setup + bddc_solve of
+ * that problem alone with the same options: the kernel's arithmetic for one
+ * instance does not depend on the other instances of its batch.
+ *
+ * A request that fails (invalid input, setup failure, no convergence) reports
+ * its own error code and does not fail the other requests of its batch.
+ * All request and result arrays are host memory.  One host thread at a time
+ * may call the functions of one server. */
+#define BDDC_PENDING 1 /* bddc_poll / bddc_wait: the request is not done yet */
+
+typedef struct bddc_server bddc_server;
+
+typedef struct {
+    double queue_ms;   /* submission -> the host setup of its batch starts */
+    double setup_ms;   /* host setup + wait for HBM admission + upload of its batch */
+    double solve_ms;   /* solve of its batch on the GPU, result copies included */
+    double latency_ms; /* submission -> result available */
+    int batch_size;    /* requests solved in the same launch, itself included */
+    int64_t batch_id;
+} bddc_request_info;
+
+typedef struct {
+    int64_t submitted, completed, failed, batches;
+    size_t device_bytes_in_use, device_bytes_peak; /* of the batches set up or solving */
+} bddc_server_info;
+
+/* opt as for bddc_setup (NULL: defaults); hbm_budget_bytes > 0 bounds the
+ * device memory of the batches on the device at a time (a batch larger than
+ * the budget on its own fails its requests with BDDC_E_OOM); max_batch >= 1.
+ * Uses the current CUDA device. */
+int bddc_server_create(const bddc_options* opt, size_t hbm_budget_bytes, int max_batch, bddc_server** out);
+
+/* inst: the problem (as for bddc_setup); f: n_cells sources; bc_value:
+ * n_faces boundary values; tol > 0.  The arrays are copied before the call
+ * returns.  *ticket identifies the request. */
+int bddc_submit(bddc_server* s, const bddc_instance* inst, const double* f, const double* bc_value, double tol,
+                uint64_t* ticket);
+
+/* BDDC_PENDING if the request is not done; otherwise copies its results
+ * (flux: n_faces, pressure: n_cells, iterations, stats, info; any may be
+ * NULL), releases the ticket and returns the request's status: BDDC_OK or
+ * its error code (BDDC_E_NOT_CONVERGED: the outputs hold the last iterate).
+ * An unknown or released ticket: BDDC_E_INVALID_ARG. */
+int bddc_poll(bddc_server* s, uint64_t ticket, double* flux, double* pressure, int* iterations, bddc_stats* stats,
+              bddc_request_info* info);
+
+/* Waits until the request is done (BDDC_OK) or timeout_s seconds passed
+ * (BDDC_PENDING); timeout_s < 0 waits without limit. */
+int bddc_wait(bddc_server* s, uint64_t ticket, double timeout_s);
+
+int bddc_server_get_info(bddc_server* s, bddc_server_info* info);
+
+/* Drops the requests not yet set up, lets the batches on the device finish,
+ * stops the threads and frees everything. */
+void bddc_server_destroy(bddc_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ BDDC_E_BREAKDOWN = -6
 BDDC_E_TIMEOUT = -7
 BDDC_E_CUDA = -8
 BDDC_E_SETUP = -9
+BDDC_PENDING = 1
 BDDC_PREC_FP64 = 0
 BDDC_PREC_FP32 = 1
 BDDC_SCALING_MULTIPLICITY = 0
@@ -51,6 +52,17 @@ class bddc_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("kappa", C.c_double),
                 ("relres", C.c_double), ("omega_tilde", C.c_double), ("n_subdomains", C.c_int),
                 ("n_interface", C.c_int), ("n_coarse", C.c_int), ("n_adaptive", C.c_int)]
+
+
+class bddc_request_info(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("latency_ms", C.c_double), ("batch_size", C.c_int), ("batch_id", C.c_int64)]
+
+
+class bddc_server_info(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("batches", C.c_int64), ("device_bytes_in_use", C.c_size_t),
+                ("device_bytes_peak", C.c_size_t)]
 
 
 class BDDCError(RuntimeError):
@@ -86,6 +98,12 @@ def _load():
         "bddc_last_error": (C.c_char_p, [P]),
         "bddc_error_string": (C.c_char_p, [C.c_int]),
         "bddc_destroy": (None, [P]),
+        "bddc_server_create": (C.c_int, [P, C.c_size_t, C.c_int, P]),
+        "bddc_submit": (C.c_int, [P, P, P, P, C.c_double, P]),
+        "bddc_poll": (C.c_int, [P, C.c_uint64, P, P, P, P, P]),
+        "bddc_wait": (C.c_int, [P, C.c_uint64, C.c_double]),
+        "bddc_server_get_info": (C.c_int, [P, P]),
+        "bddc_server_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -101,7 +119,9 @@ EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats"
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
             "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_debug_phase_times",
             "bddc_last_error",
-            "bddc_error_string", "bddc_destroy")
+            "bddc_error_string", "bddc_destroy",
+            "bddc_server_create", "bddc_submit", "bddc_poll", "bddc_wait", "bddc_server_get_info",
+            "bddc_server_destroy")
 
 
 def error_string(code: int) -> str:
@@ -304,6 +324,64 @@ class HostSetup:
     def close(self):
         if getattr(self, "_h", None):
             lib.bddc_host_setup_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Server:
+    """Serving loop (bddc_server_*): requests of any size submitted as they
+    arrive, solved in batches by the library's own setup and solve threads."""
+
+    def __init__(self, options=None, hbm_budget_bytes=8 << 30, max_batch=64):
+        o = options if options is not None else default_options()
+        h = C.c_void_p()
+        rc = lib.bddc_server_create(C.byref(o), int(hbm_budget_bytes), int(max_batch), C.byref(h))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, "server_create")
+        self._h = h
+        self._sizes = {}
+
+    def submit(self, pb, f=None, bc_value=None, tol=1e-8) -> int:
+        """Copy one problem (a ``synth.Problem``-like object) into the queue."""
+        keep = _Keep([pb])
+        fv = np.ascontiguousarray(pb.f if f is None else f, dtype=np.float64)
+        bv = np.ascontiguousarray(pb.bc_value if bc_value is None else bc_value, dtype=np.float64)
+        t = C.c_uint64()
+        rc = lib.bddc_submit(self._h, C.byref(keep.inst[0]), fv.ctypes.data, bv.ctypes.data, float(tol),
+                             C.byref(t))
+        if rc != BDDC_OK:
+            raise BDDCError(rc, "submit")
+        self._sizes[t.value] = (pb.grid.n_cells, len(pb.bc_type))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, flux, pressure, iterations, stats, info)."""
+        nc, nf = self._sizes[ticket]
+        flux = np.empty(nf)
+        pres = np.empty(nc)
+        it = C.c_int()
+        st = bddc_stats()
+        info = bddc_request_info()
+        rc = lib.bddc_poll(self._h, C.c_uint64(ticket), flux.ctypes.data, pres.ctypes.data, C.byref(it),
+                           C.byref(st), C.byref(info))
+        if rc == BDDC_PENDING:
+            return None
+        del self._sizes[ticket]
+        return rc, flux, pres, it.value, st, info
+
+    def wait(self, ticket, timeout_s=-1.0) -> bool:
+        return lib.bddc_wait(self._h, C.c_uint64(ticket), float(timeout_s)) == BDDC_OK
+
+    def info(self) -> bddc_server_info:
+        out = bddc_server_info()
+        lib.bddc_server_get_info(self._h, C.byref(out))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.bddc_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

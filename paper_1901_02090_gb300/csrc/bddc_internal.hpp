@@ -69,4 +69,11 @@ struct SetupResult {
 
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& out);
 
+// device part of bddc_setup (bddc_kernels.cu): uploads the host setup of a
+// batch, sizes the persistent launch, and returns the handle
+int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_stream, Packed&& packed,
+                      bddc_handle** out);
+// device memory held by a handle (bytes)
+size_t handle_device_bytes(const bddc_handle* h);
+
 }  // namespace bddc

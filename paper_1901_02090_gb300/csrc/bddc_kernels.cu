@@ -1031,6 +1031,7 @@ struct bddc_handle {
     Packed P;
     Params prm{};
     std::vector<void*> allocs;
+    size_t dev_bytes = 0;  // device memory held by the handle
     std::string err;
     mutable std::vector<bddc_stats> stats;  // kappa filled on demand (bddc_get_stats)
     mutable bool kappa_stale = false;       // the last solve's kappa is not computed yet
@@ -1070,6 +1071,7 @@ int upload(bddc_handle* h, const std::vector<T>& v, const T** out) {
     void* p = nullptr;
     if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) return BDDC_E_OOM;
     h->allocs.push_back(p);
+    h->dev_bytes += v.size() * sizeof(T);
     if (cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return BDDC_E_CUDA;
     *out = static_cast<const T*>(p);
     return BDDC_OK;
@@ -1080,6 +1082,7 @@ int dalloc(bddc_handle* h, size_t n, T** out) {
     void* p = nullptr;
     if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return BDDC_E_OOM;
     h->allocs.push_back(p);
+    h->dev_bytes += std::max<size_t>(n, 1) * sizeof(T);
     cudaMemset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
     *out = static_cast<T*>(p);
     return BDDC_OK;
@@ -1144,18 +1147,32 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
         cudaGetLastError();
         return BDDC_E_CUDA;
     }
+    Packed P;
+    SetupResult r = build_all(n_instances, inst, opt, P);
+    if (r.code) {
+        g_setup_err = r.msg;
+        return r.code;
+    }
+    return bddc::setup_from_packed(n_instances, opt, cuda_stream, std::move(P), out);
+}
+
+}  // extern "C"
+
+namespace bddc {
+
+size_t handle_device_bytes(const bddc_handle* h) { return h ? h->dev_bytes : 0; }
+
+// device part of bddc_setup: upload a batch's host setup and size the launch
+int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_stream, Packed&& packed,
+                      bddc_handle** out) {
+    *out = nullptr;
     bddc_handle* h = new bddc_handle();
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&h->device);
     h->n_inst = n_instances;
     h->maxit = opt.maxit;
     h->precision = opt.precision;
-    SetupResult r = build_all(n_instances, inst, opt, h->P);
-    if (r.code) {
-        g_setup_err = r.msg;
-        delete h;
-        return r.code;
-    }
+    h->P = std::move(packed);
     Packed& P = h->P;
     for (int b = 0; b < n_instances; ++b) {
         h->total_cells += P.inst_ncells[b];
@@ -1330,6 +1347,10 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     return BDDC_OK;
 }
 
+}  // namespace bddc
+
+extern "C" {
+
 int bddc_sizes(const bddc_handle* h, int* n_instances, int64_t* n_interface, int64_t* n_subdomains) {
     if (!h) return BDDC_E_INVALID_ARG;
     if (n_instances) *n_instances = h->n_inst;
@@ -1352,7 +1373,10 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     auto stage = [&](const double* src, size_t n, double** buf, bool copy_in) -> const double* {
         if (is_device_ptr(src)) return src;
         if (!*buf && cudaMalloc((void**)buf, n * sizeof(double)) != cudaSuccess) { rc = BDDC_E_OOM; return nullptr; }
-        if (std::find(h->allocs.begin(), h->allocs.end(), (void*)*buf) == h->allocs.end()) h->allocs.push_back(*buf);
+        if (std::find(h->allocs.begin(), h->allocs.end(), (void*)*buf) == h->allocs.end()) {
+            h->allocs.push_back(*buf);
+            h->dev_bytes += n * sizeof(double);
+        }
         if (copy_in) cudaMemcpyAsync(*buf, src, n * sizeof(double), cudaMemcpyHostToDevice, st);
         return *buf;
     };

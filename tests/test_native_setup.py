@@ -162,6 +162,26 @@ def test_setup_without_gpu_reports_cuda_error_not_crash():
     assert e.value.code == bddc.BDDC_E_CUDA
 
 
+def test_server_without_gpu_and_invalid_arguments():
+    """The serving entry points validate their arguments on the host; without
+    a GPU server creation returns BDDC_E_CUDA instead of starting threads."""
+    import ctypes as C
+    import torch
+    lib = bddc.lib
+    out = C.c_void_p()
+    o = bddc.default_options()
+    assert lib.bddc_server_create(C.byref(o), 0, 4, C.byref(out)) == bddc.BDDC_E_INVALID_ARG
+    assert lib.bddc_server_create(C.byref(o), 1 << 30, 0, C.byref(out)) == bddc.BDDC_E_INVALID_ARG
+    assert lib.bddc_server_create(C.byref(o), 1 << 30, 4, None) == bddc.BDDC_E_INVALID_ARG
+    t = C.c_uint64()
+    assert lib.bddc_submit(None, None, None, None, 1e-8, C.byref(t)) == bddc.BDDC_E_INVALID_ARG
+    assert lib.bddc_poll(None, 1, None, None, None, None, None) == bddc.BDDC_E_INVALID_ARG
+    assert lib.bddc_wait(None, 1, 0.0) == bddc.BDDC_E_INVALID_ARG
+    lib.bddc_server_destroy(None)
+    if not torch.cuda.is_available():
+        assert lib.bddc_server_create(C.byref(o), 1 << 30, 4, C.byref(out)) == bddc.BDDC_E_CUDA
+
+
 @pytest.mark.parametrize("case", ["c1", "irregular2d", "c1_wells_pure_flux"])
 def test_mixed_precision_emulation_keeps_balance_and_accuracy(case):
     """FP32 correction operator and coarse basis (the mixed path): with the
