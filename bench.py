@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--single-solves", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the serving stream (0: skip it)")
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrival rate of the stream (1/s)")
     return ap.parse_args()
 
 
@@ -233,6 +236,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_run(args, rank):
+    """The serving stream: independent 2D channelized fields of 30-60 x
+    110-220 cells (10 x 10-cell subdomains, random pressure-drop direction)
+    arriving as a seeded Poisson process, submitted to the library's serving
+    loop (continuous batching, admission by HBM footprint).  Reports solves/s
+    over the stream and the p50/p99 of submission-to-result latency, which
+    includes each request's own setup."""
+    from paper_1901_02090_gb300 import bddc
+    from synth.problems import serving_request
+    n, rate = args.serving_requests, args.serving_rate
+    pbs = [serving_request(rank * 1000003 + i) for i in range(n)]
+    gaps = np.random.default_rng(7 + rank).exponential(1.0 / rate, size=n)
+    srv = bddc.Server(bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32),
+                      hbm_budget_bytes=16 << 30, max_batch=64)
+    pending, lat, its, batches = [], [], [], set()
+    t0 = time.perf_counter()
+    t_next = t0
+    for i, pb in enumerate(pbs):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+        pending.append(srv.submit(pb, tol=args.tol))
+    failed = 0
+    for t in pending:
+        srv.wait(t)
+        rc, _, _, it, _, info = srv.poll(t)
+        failed += rc != bddc.BDDC_OK
+        lat.append(info.latency_ms)
+        its.append(it)
+        batches.add(info.batch_id)
+    wall = time.perf_counter() - t0
+    peak = srv.info().device_bytes_peak
+    srv.close()
+    lat = np.array(lat)
+    return {"value": n / wall, "unit": "solves/s", "requests": n, "arrival_rate_per_s": rate,
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "failed": int(failed), "batches": len(batches), "mean_batch": n / max(1, len(batches)),
+            "iterations_mean": float(np.mean(its)), "device_bytes_peak": int(peak),
+            "workload": "30-60 x 110-220 channelized fields, 10x10-cell subdomains, random pressure direction, "
+                        "tau=%g, mixed path; latency includes each request's host setup" % args.tau}
+
+
 def single_path(args, pb1, dev, stream):
     """The plain FP64 path, one solve per launch: solves/s and p50/p99 latency."""
     import torch
@@ -343,6 +388,8 @@ def main():
     if args.single_solves > 0:
         fp64_single = single_path(args, pbs[0], dev, stream)
 
+    serving = serving_run(args, rank) if args.serving_requests > 0 else None
+
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
@@ -360,6 +407,7 @@ def main():
         "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
         "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
         "fp64_single": fp64_single,
+        "serving": serving,
         "latency_batched_ms": {"p50": float(np.percentile(kms, 50)), "p99": float(np.percentile(kms, 99)),
                                "per_step_wall": total_ms / K, "note": "kernel time of one batch (CUDA events)"},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(8 * (len(f_h) + len(bc_h))),
