@@ -226,6 +226,11 @@ int bddc_last_solve_timing(const bddc_handle* h, double* kernel_ms, double* algo
 typedef struct bddc_host_setup bddc_host_setup;
 int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt,
                            bddc_host_setup** out);
+/* The same, with the dense part of the local maps (S, G_pre, G_post) computed
+ * on the current CUDA device, as bddc_setup and the serving loop do; they
+ * agree with the host computation to rounding.  BDDC_E_CUDA without a GPU. */
+int bddc_host_setup_create_gpu(int n_instances, const bddc_instance* inst, const bddc_options* opt,
+                               bddc_host_setup** out);
 int bddc_host_setup_query(const bddc_host_setup* hs, const char* name, int64_t* count, int* elem_bytes);
 int bddc_host_setup_copy(const bddc_host_setup* hs, const char* name, void* dst);
 void bddc_host_setup_destroy(bddc_host_setup* hs);

@@ -90,6 +90,7 @@ def _load():
         "bddc_subassembled_apply_noalloc": (C.c_int, [C.c_int, P, P, P, P, P, P, C.c_int64, P, P, P]),
         "bddc_last_solve_timing": (C.c_int, [P, P, P]),
         "bddc_host_setup_create": (C.c_int, [C.c_int, P, P, P]),
+        "bddc_host_setup_create_gpu": (C.c_int, [C.c_int, P, P, P]),
         "bddc_host_setup_query": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
         "bddc_host_setup_destroy": (None, [P]),
@@ -116,7 +117,7 @@ lib = _load()
 EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
             "bddc_subassembled_apply_noalloc",
-            "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_query",
+            "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_create_gpu", "bddc_host_setup_query",
             "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_debug_phase_times",
             "bddc_last_error",
             "bddc_error_string", "bddc_destroy",
@@ -291,11 +292,13 @@ class HostSetup:
 
     _DT = {4: np.int32, 8: None}
 
-    def __init__(self, problems, options=None):
+    def __init__(self, problems, options=None, device=False):
+        """device=True: the dense local maps on the GPU (the path of bddc_setup)."""
         keep = _Keep(list(problems))
         h = C.c_void_p()
         opt = options if options is not None else default_options()
-        rc = lib.bddc_host_setup_create(len(keep.inst), keep.inst, C.byref(opt), C.byref(h))
+        create = lib.bddc_host_setup_create_gpu if device else lib.bddc_host_setup_create
+        rc = create(len(keep.inst), keep.inst, C.byref(opt), C.byref(h))
         if rc != BDDC_OK:
             raise BDDCError(rc, lib.bddc_last_error(None).decode())
         self._h = h

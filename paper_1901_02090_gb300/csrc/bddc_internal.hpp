@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,10 @@ struct Packed {
     std::vector<double> S, F64, P64, Gpre, Gpost, Kinv;
     std::vector<float> F32, P32;
     int precision = BDDC_PREC_FP64;
+    // G_post computed on the GPU stays there: a device array in the layout
+    // of Gpost (which is then empty on the host), freed with its last owner
+    std::shared_ptr<double> dev_Gpost;
+    int64_t dev_Gpost_count = 0;
     int64_t n_sub = 0, n_gamma = 0, n_coarse_vec = 0;
     int max_ng = 0, max_m = 0, max_ncn = 0, max_out_post = 0, max_in_post = 0;
 };
@@ -67,7 +72,43 @@ struct SetupResult {
     std::string msg;
 };
 
-SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& out);
+// Dense part of the local maps of a batch of subdomains (the interior saddle
+// solves behind S^i, G_pre and G_post, with iterative refinement), for the
+// device implementation in bddc_setup_gpu.cu.  Per-subdomain blocks are
+// concatenated; o_* are prefix offsets with n_sub + 1 entries.
+struct LocalMapsBatch {
+    int n_sub = 0;
+    // per subdomain
+    std::vector<int> dim, ng, ni, nc;
+    std::vector<double> vol, d;
+    std::vector<int64_t> o_cell, o_ng, o_ni, o_ch;
+    // per cell and axis (stride 3): local lower / upper face (-1 absent) and h_a^2/|c|/k_a
+    std::vector<int> clo, chi;
+    std::vector<double> cs;
+    // per interface dof: its cell, axis and side (0 lower, 1 upper)
+    std::vector<int> gcell, gaxis, gside;
+    // per interior dof, in chain order: interior index and Thomas factors;
+    // per chain (o_ch, n_chains + 1 entries per subdomain): start position
+    std::vector<int> order, cstart;
+    std::vector<double> dfac, lfac, off;
+    // outputs, in the layouts of the host setup
+    std::vector<int64_t> o_S, o_Gpre, o_Gpost;
+    std::vector<double> S, GpreT;
+    std::shared_ptr<double> dev_GpostT;  // G_post of every subdomain, on the device (o_Gpost layout)
+    std::vector<int> status;  // per subdomain: BDDC_OK or BDDC_E_SETUP
+};
+
+// host copy of a device array of doubles (for the host-side export)
+bool device_to_host(const double* dev, int64_t n, double* host);
+using LocalMapsDevice = int (*)(LocalMapsBatch& batch, std::string& err);
+
+// computes a batch's dense local maps on the current CUDA device
+int local_maps_device(LocalMapsBatch& batch, std::string& err);
+
+// host setup of a batch; with a device hook the dense part of the local
+// maps runs there
+SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& out,
+                      LocalMapsDevice device = nullptr);
 
 // device part of bddc_setup (bddc_kernels.cu): uploads the host setup of a
 // batch, sizes the persistent launch, and returns the handle

@@ -997,6 +997,15 @@ __global__ void __launch_bounds__(kThreads) k_precond_prolong(Params p, double* 
     }
 }
 
+// FP64 -> FP32 pair (hi, lo) elementwise, on the device
+__global__ void k_pairs(int64_t n, const double* src, float2* dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        const float hi = __double2float_rn(v);
+        dst[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
 // raw subassembled apply (no handle)
 __global__ void __launch_bounds__(128) k_subassembled_local(int n_sub, const int* ng_arr, const int64_t* slot_off,
                                                             const int64_t* S_off, const double* S, const int* gidx,
@@ -1148,7 +1157,7 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
         return BDDC_E_CUDA;
     }
     Packed P;
-    SetupResult r = build_all(n_instances, inst, opt, P);
+    SetupResult r = build_all(n_instances, inst, opt, P, local_maps_device);  // dense local maps on the GPU
     if (r.code) {
         g_setup_err = r.msg;
         return r.code;
@@ -1202,7 +1211,13 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     UP(slot_dsig, P.slot_dsig); UP(cslot_c, P.cslot_c); UP(cell_gid, P.cell_gid); UP(int_fid, P.int_fid);
     UP(g_fid, P.g_fid); UP(g_bsign, P.g_bsign); UP(c_slot_a, P.c_slot_a); UP(c_slot_b, P.c_slot_b);
     UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0);
-    UP(Gpre, P.Gpre); UP(Gpost, P.Gpost); UP(P64, P.P64);
+    UP(Gpre, P.Gpre); UP(P64, P.P64);
+    if (P.dev_Gpost) {  // computed on the device by the setup: adopted, freed with the handle's Packed
+        p.Gpost = P.dev_Gpost.get();
+        h->dev_bytes += sizeof(double) * (size_t)P.dev_Gpost_count;
+    } else {
+        UP(Gpost, P.Gpost);
+    }
     UP(slot_fcs, P.slot_fcs); UP(cslot_n, P.cslot_n); UP(slot_coef, P.slot_coef);
     UP(slot_fperm, P.slot_fperm); UP(cslot_fstart, P.cslot_fstart); UP(slot_fcoefp, P.slot_fcoefp);
     {
@@ -1242,7 +1257,27 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
             if (!rc) rc = upload(h, P.P32, &pp);
             if (!rc) rc = upload(h, pairs(P.S), &s2);
             if (!rc) rc = upload(h, pairs(P.Kinv), &k2);
-            if (!rc) rc = upload(h, pairs(P.Gpost), &p.Gpost2);
+            if (!rc) {
+                if (P.dev_Gpost) {
+                    // written in full by k_pairs on the handle's stream: no zeroing
+                    float2* g2 = nullptr;
+                    if (cudaMalloc((void**)&g2, std::max<int64_t>(P.dev_Gpost_count, 1) * sizeof(float2)) != cudaSuccess) {
+                        cudaGetLastError();
+                        rc = BDDC_E_OOM;
+                    } else {
+                        h->allocs.push_back(g2);
+                        h->dev_bytes += sizeof(float2) * (size_t)P.dev_Gpost_count;
+                    }
+                    if (!rc) {
+                        const int64_t cnt = P.dev_Gpost_count;
+                        k_pairs<<<(int)std::min<int64_t>((cnt + 255) / 256, 65536), 256, 0, h->stream>>>(cnt, p.Gpost, g2);
+                        if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = BDDC_E_CUDA;
+                    }
+                    p.Gpost2 = g2;
+                } else {
+                    rc = upload(h, pairs(P.Gpost), &p.Gpost2);
+                }
+            }
             p.F = f;
             p.P = pp;
             p.S = s2;
@@ -1339,7 +1374,9 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     h->bytes_iter = it_b;
     h->bytes_pre = pre_b;
     h->bytes_post = post_b;
-    if (cudaGetLastError() != cudaSuccess) {
+    // the uploads and the zeroing of the work vectors ran on the legacy
+    // default stream; a non-blocking solve stream does not wait for it
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         bddc_destroy(h);
         return BDDC_E_CUDA;
     }

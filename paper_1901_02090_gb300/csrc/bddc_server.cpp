@@ -3,8 +3,9 @@
 //
 // Two host threads per server:
 //   setup thread  takes the queued requests in arrival order (consecutive
-//                 requests with equal tol, at most max_batch), runs the host
-//                 setup of the batch (bddc::build_all), waits until the
+//                 requests with equal tol, at most max_batch), runs the
+//                 setup of the batch (bddc::build_all, the dense local maps
+//                 on the GPU), waits until the
 //                 batch's device footprint fits the HBM budget beside the
 //                 batches already admitted, uploads it (bddc::setup_from_packed)
 //                 and hands it to the solve thread;
@@ -97,8 +98,10 @@ size_t estimate_device_bytes(const bddc::Packed& P, const bddc_options& opt, int
     b += bytes(P.c_slot_a) * 2;
     b += bytes(P.S) + bytes(P.F64) + bytes(P.F32) + bytes(P.P64) + bytes(P.P32) + bytes(P.Gpre) + bytes(P.Gpost);
     b += bytes(P.Kinv) + 8 * (size_t)n_inst * (size_t)P.max_ncn;  // row padding
+    const size_t gpost = bytes(P.Gpost) + 8 * (size_t)P.dev_Gpost_count;  // on the host or already on the device
+    b += 8 * (size_t)P.dev_Gpost_count;
     if (opt.precision == BDDC_PREC_FP32) {
-        b += bytes(P.Gpost);                          // G_post as FP32 pairs
+        b += gpost;                                   // G_post as FP32 pairs
         // weights, d*sigma and 1/n as FP32 pairs; coefficients as FP32
         b += bytes(P.slot_w) + bytes(P.slot_dsig) + bytes(P.cslot_n) * 2 + bytes(P.slot_coef) / 2 +
              bytes(P.slot_fcoefp) / 2;
@@ -154,14 +157,14 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
     std::vector<bddc_instance> inst;
     for (auto& r : reqs) inst.push_back(r->instance());
     bddc::Packed P;
-    bddc::SetupResult res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P);
+    bddc::SetupResult res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device);
     if (res.code) {
         // find the failing requests: each alone; the others are set up again together
         std::vector<ReqPtr> ok;
         for (auto& r : reqs) {
             bddc::Packed Q;
             const bddc_instance one = r->instance();
-            const bddc::SetupResult rr = bddc::build_all(1, &one, s->opt, Q);
+            const bddc::SetupResult rr = bddc::build_all(1, &one, s->opt, Q, bddc::local_maps_device);
             if (rr.code) finish(s, r, rr.code);
             else ok.push_back(r);
         }
@@ -170,7 +173,7 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
         inst.clear();
         for (auto& r : reqs) inst.push_back(r->instance());
         P = bddc::Packed();
-        res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P);
+        res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device);
         if (res.code) {
             for (auto& r : reqs) finish(s, r, res.code);
             return;

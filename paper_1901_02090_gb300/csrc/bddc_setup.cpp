@@ -397,9 +397,15 @@ void chain_solve(const Chains& ch, double* x) {
     }
 }
 
-SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
+// the cheap part of the local maps: pressure scaling d, sigma, the cell /
+// axis / side of every interface dof, and the Thomas factors of A_II
+struct LocalPre {
+    std::vector<int> gcell, gaxis, gside;
+    Chains ch;
+};
+
+void local_prologue(const Inst& I, Sub& S, bool pressure_scaling, LocalPre& pre) {
     const int dim = I.geo.dim, ng = S.ng, ni = S.ni, nc = S.nc;
-    const double vol = I.geo.vol;
     // diag(A^i) and the pressure scaling d_i (reading: mean of the local
     // unassembled diagonal over all local flux dofs)
     std::vector<double> diagA(ng + ni, 0.0);
@@ -413,7 +419,6 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
     double sum = 0.0;
     for (double v : diagA) sum += v;
     S.d = (pressure_scaling && ng + ni > 0) ? sum / (ng + ni) : 1.0;
-    const double d = S.d;
     S.diagA.assign(diagA.begin(), diagA.begin() + ng);
     // sigma = (B^i)^T 1 on interface dofs; the interface dof's cell and side
     std::vector<int> gcell(ng, -1), gaxis(ng, 0), gside(ng, 0);
@@ -425,9 +430,20 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
         }
     S.sigma.resize(ng);
     for (int k = 0; k < ng; ++k) S.sigma[k] = gside[k] == 0 ? 1.0 : -1.0;
+    build_chains(S, dim, pre.ch);
+    pre.gcell.swap(gcell);
+    pre.gaxis.swap(gaxis);
+    pre.gside.swap(gside);
+}
 
-    Chains ch;
-    build_chains(S, dim, ch);
+SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
+    const int dim = I.geo.dim, ng = S.ng, ni = S.ni, nc = S.nc;
+    const double vol = I.geo.vol;
+    LocalPre pre;
+    local_prologue(I, S, pressure_scaling, pre);
+    const double d = S.d;
+    const Chains& ch = pre.ch;
+    const std::vector<int>&gcell = pre.gcell, &gaxis = pre.gaxis, &gside = pre.gside;
     // Y = A_II^{-1} dB_I^T (ni x nc, column-major per cell)
     std::vector<double> Y((size_t)nc * ni, 0.0);
     for (int r = 0; r < nc; ++r) {
@@ -942,14 +958,89 @@ static void symmetrize(std::vector<double>& M, int n) {
         }
 }
 
-SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P) {
+// the dense part of the local maps of every subdomain on the device: host
+// prologues (in parallel), one batch, outputs back into the subdomains
+SetupResult device_local_maps(std::vector<Inst>& I, const std::vector<std::pair<int, int>>& tasks, bool ps,
+                              int nthreads, LocalMapsDevice device, std::shared_ptr<double>& dev_gpost,
+                              int64_t& dev_gpost_count) {
+    const int n = (int)tasks.size();
+    std::vector<LocalPre> pre(n);
+    parallel_for(n, nthreads, [&](int64_t t) {
+        auto [b, s] = tasks[t];
+        local_prologue(I[b], I[b].subs[s], ps, pre[t]);
+    });
+    LocalMapsBatch B;
+    B.n_sub = n;
+    for (auto* v : {&B.o_cell, &B.o_ng, &B.o_ni, &B.o_ch, &B.o_S, &B.o_Gpre, &B.o_Gpost}) v->assign(n + 1, 0);
+    for (int t = 0; t < n; ++t) {
+        auto [b, s] = tasks[t];
+        const Sub& S = I[b].subs[s];
+        const int dim = I[b].geo.dim;
+        B.dim.push_back(dim);
+        B.ng.push_back(S.ng);
+        B.ni.push_back(S.ni);
+        B.nc.push_back(S.nc);
+        B.vol.push_back(I[b].geo.vol);
+        B.d.push_back(S.d);
+        for (int r = 0; r < S.nc; ++r)
+            for (int a = 0; a < 3; ++a) {
+                B.clo.push_back(a < dim ? S.clo[(size_t)r * dim + a] : -1);
+                B.chi.push_back(a < dim ? S.chi[(size_t)r * dim + a] : -1);
+                B.cs.push_back(a < dim ? S.cs[(size_t)r * dim + a] : 0.0);
+            }
+        B.gcell.insert(B.gcell.end(), pre[t].gcell.begin(), pre[t].gcell.end());
+        B.gaxis.insert(B.gaxis.end(), pre[t].gaxis.begin(), pre[t].gaxis.end());
+        B.gside.insert(B.gside.end(), pre[t].gside.begin(), pre[t].gside.end());
+        const Chains& ch = pre[t].ch;
+        B.order.insert(B.order.end(), ch.order.begin(), ch.order.end());
+        B.dfac.insert(B.dfac.end(), ch.dfac.begin(), ch.dfac.end());
+        B.lfac.insert(B.lfac.end(), ch.lfac.begin(), ch.lfac.end());
+        B.off.insert(B.off.end(), ch.off.begin(), ch.off.end());
+        B.cstart.insert(B.cstart.end(), ch.start.begin(), ch.start.end());
+        const int64_t ncol = S.ng + S.nc;
+        B.o_cell[t + 1] = B.o_cell[t] + S.nc;
+        B.o_ng[t + 1] = B.o_ng[t] + S.ng;
+        B.o_ni[t + 1] = B.o_ni[t] + S.ni;
+        B.o_ch[t + 1] = B.o_ch[t] + (int64_t)ch.start.size();
+        B.o_S[t + 1] = B.o_S[t] + (int64_t)S.ng * S.ng;
+        B.o_Gpre[t + 1] = B.o_Gpre[t] + (int64_t)S.nc * S.ng;
+        B.o_Gpost[t + 1] = B.o_Gpost[t] + ncol * (S.ni + S.nc);
+    }
+    std::string err;
+    const int rc = device(B, err);
+    if (rc) return {rc, "device local maps: " + err};
+    for (int t = 0; t < n; ++t) {
+        auto [b, s] = tasks[t];
+        Sub& S = I[b].subs[s];
+        if (B.status[t] != BDDC_OK)
+            return {B.status[t], "instance " + std::to_string(b) + " subdomain " + std::to_string(s) +
+                                     ": singular local pressure Schur complement"};
+        S.S.assign(B.S.begin() + B.o_S[t], B.S.begin() + B.o_S[t + 1]);
+        S.GpreT.assign(B.GpreT.begin() + B.o_Gpre[t], B.GpreT.begin() + B.o_Gpre[t + 1]);
+        const int ng = S.ng;
+        for (int a = 0; a < ng; ++a)  // symmetrise S^i (rounding only)
+            for (int c = a + 1; c < ng; ++c) {
+                const double v = 0.5 * (S.S[(size_t)a * ng + c] + S.S[(size_t)c * ng + a]);
+                S.S[(size_t)a * ng + c] = S.S[(size_t)c * ng + a] = v;
+            }
+    }
+    dev_gpost = B.dev_GpostT;  // G_post stays on the device, in the packed layout
+    dev_gpost_count = B.o_Gpost[n];
+    return {};
+}
+
+SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P,
+                      LocalMapsDevice device) {
     const int nthreads = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     std::vector<Inst> I(n_inst);
-    for (int b = 0; b < n_inst; ++b) {
-        SetupResult r = read_instance(inst[b], I[b]);
-        if (r.code) { r.msg = "instance " + std::to_string(b) + ": " + r.msg; return r; }
-        r = build_topology(I[b]);
-        if (r.code) { r.msg = "instance " + std::to_string(b) + ": " + r.msg; return r; }
+    {
+        std::vector<SetupResult> rr(n_inst);
+        parallel_for(n_inst, nthreads, [&](int64_t b) {
+            rr[b] = read_instance(inst[b], I[b]);
+            if (!rr[b].code) rr[b] = build_topology(I[b]);
+        });
+        for (int b = 0; b < n_inst; ++b)
+            if (rr[b].code) { rr[b].msg = "instance " + std::to_string(b) + ": " + rr[b].msg; return rr[b]; }
     }
     // flat task list over all subdomains
     std::vector<std::pair<int, int>> tasks;
@@ -961,12 +1052,20 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         std::lock_guard<std::mutex> lk(mu);
         if (!err.code) err = {r.code, "instance " + std::to_string(b) + " subdomain " + std::to_string(s) + ": " + r.msg};
     };
-    parallel_for((int64_t)tasks.size(), nthreads, [&](int64_t t) {
-        auto [b, s] = tasks[t];
-        SetupResult r = local_maps(I[b], I[b].subs[s], opt.pressure_scaling != 0);
-        if (r.code) fail(r, b, s);
-    });
-    if (err.code) return err;
+    std::shared_ptr<double> dev_gpost;
+    int64_t dev_gpost_count = 0;
+    if (device) {
+        SetupResult r = device_local_maps(I, tasks, opt.pressure_scaling != 0, nthreads, device, dev_gpost,
+                                          dev_gpost_count);
+        if (r.code) return r;
+    } else {
+        parallel_for((int64_t)tasks.size(), nthreads, [&](int64_t t) {
+            auto [b, s] = tasks[t];
+            SetupResult r = local_maps(I[b], I[b].subs[s], opt.pressure_scaling != 0);
+            if (r.code) fail(r, b, s);
+        });
+        if (err.code) return err;
+    }
     for (int b = 0; b < n_inst; ++b) weights(I[b], opt.scaling);
     const bool adaptive = opt.tau > 0 && std::isfinite(opt.tau);
     // Cholesky of every S^i (the face problems need (S^i)^{-1}); always done
@@ -1016,6 +1115,8 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     // ---- pack -----------------------------------------------------------------
     P = Packed();
     P.precision = opt.precision;
+    P.dev_Gpost = dev_gpost;  // set: G_post is on the device and P.Gpost stays empty
+    P.dev_Gpost_count = dev_gpost_count;
     int64_t goff = 0, coff = 0, kinv_off = 0, s_glob = 0, face_off = 0, cell_off = 0;
     int64_t slot = 0, cslot = 0, celll = 0, intl = 0;
     int64_t oS = 0, oF = 0, oP = 0, oGpre = 0, oGpost = 0;
@@ -1085,7 +1186,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             oP += pad4(nP);
             P.Gpre.insert(P.Gpre.end(), S.GpreT.begin(), S.GpreT.end());
             oGpre += (int64_t)S.nc * S.ng;
-            P.Gpost.insert(P.Gpost.end(), S.GpostT.begin(), S.GpostT.end());
+            if (!P.dev_Gpost) P.Gpost.insert(P.Gpost.end(), S.GpostT.begin(), S.GpostT.end());
             oGpost += (int64_t)(S.ng + S.nc) * (S.ni + S.nc);
             for (int k = 0; k < S.ng; ++k) {
                 const int g = S.gidx[k];
@@ -1157,6 +1258,11 @@ bool export_vec(const std::vector<T>& v, void* dst, int64_t* count, int* eb) {
 
 bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* count, int* eb) {
     const std::string n(name ? name : "");
+    if (n == "Gpost" && P.dev_Gpost) {
+        if (count) *count = P.dev_Gpost_count;
+        if (eb) *eb = 8;
+        return !dst || bddc::device_to_host(P.dev_Gpost.get(), P.dev_Gpost_count, static_cast<double*>(dst));
+    }
 #define E(x) if (n == #x) return export_vec(P.x, dst, count, eb)
     E(sub_inst); E(sub_ng); E(sub_ni); E(sub_nc); E(sub_m); E(sub_local); E(slot_g); E(slot_partner);
     E(cslot_c); E(c_slot_a); E(c_slot_b); E(g_slot_a); E(g_slot_b); E(slot_fcs); E(cslot_n); E(slot_coef); E(slot_fperm); E(cslot_fstart); E(slot_fcoefp);
@@ -1186,8 +1292,8 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
 
 extern "C" {
 
-int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt_in,
-                           bddc_host_setup** out) {
+static int host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt_in,
+                             bddc_host_setup** out, bddc::LocalMapsDevice device) {
     if (!out) return BDDC_E_INVALID_ARG;
     *out = nullptr;
     if (n_instances <= 0 || !inst) return BDDC_E_INVALID_ARG;
@@ -1195,13 +1301,23 @@ int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bdd
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
     auto* hs = new bddc_host_setup();
-    bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P);
+    bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P, device);
     if (r.code) {
         delete hs;
         return r.code;
     }
     *out = hs;
     return BDDC_OK;
+}
+
+int bddc_host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt,
+                           bddc_host_setup** out) {
+    return host_setup_create(n_instances, inst, opt, out, nullptr);
+}
+
+int bddc_host_setup_create_gpu(int n_instances, const bddc_instance* inst, const bddc_options* opt,
+                               bddc_host_setup** out) {
+    return host_setup_create(n_instances, inst, opt, out, bddc::local_maps_device);
 }
 
 int bddc_host_setup_query(const bddc_host_setup* hs, const char* name, int64_t* count, int* elem_bytes) {
