@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--tau", type=float, default=10.0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--single-solves", type=int, default=40)
@@ -156,7 +156,8 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bddc_solve_kernel_traffic_c2_batch64.txt")
+def traffic_file(batch):
+    return os.path.join(ROOT, "profiles", f"bddc_solve_kernel_traffic_c2_batch{batch}.txt")
 
 
 def kernel_source_digest():
@@ -176,10 +177,11 @@ def measured_traffic(batch):
     """DRAM bytes per launch of the solve kernel from the committed ncu
     capture of this workload, or None when absent, for another batch, or
     taken on other kernel sources."""
-    if not os.path.exists(TRAFFIC_FILE):
+    path = traffic_file(batch)
+    if not os.path.exists(path):
         return None
     kv = {}
-    for line in open(TRAFFIC_FILE):
+    for line in open(path):
         if "=" in line and not line.lstrip().startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
