@@ -161,13 +161,14 @@ def traffic_file(batch):
 
 
 def kernel_source_digest():
-    """sha256 over the solver's CUDA sources: a measured DRAM traffic figure
-    is valid only for the sources it was captured with."""
+    """sha256 over the solve kernel's CUDA sources: a measured DRAM traffic
+    figure is valid only for the sources it was captured with."""
     import hashlib
     d = os.path.join(ROOT, "paper_1901_02090_gb300", "csrc")
     h = hashlib.sha256()
+    # the solve kernel's translation unit and the headers it includes
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh")):
+        if name == "bddc_kernels.cu" or name.endswith(".cuh"):
             h.update(name.encode())
             h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()

@@ -267,6 +267,13 @@ void solve_batch(bddc_server* s, Batch& b) {
         std::copy(b.reqs[i]->f.begin(), b.reqs[i]->f.end(), f.begin() + cell_off[i]);
         std::copy(b.reqs[i]->bc_value.begin(), b.reqs[i]->bc_value.end(), bc.begin() + face_off[i]);
     }
+    for (auto& r : b.reqs) {  // the inputs are no longer needed: set up, and copied for the solve
+        std::vector<double>().swap(r->perm);
+        std::vector<double>().swap(r->f);
+        std::vector<double>().swap(r->bc_value);
+        std::vector<int32_t>().swap(r->part);
+        std::vector<int8_t>().swap(r->bc_type);
+    }
     std::vector<double> flux((size_t)face_off[n]), pres((size_t)cell_off[n]);
     std::vector<int> its(n, 0);
     const int rc = bddc_solve(b.h, f.data(), bc.data(), b.tol, flux.data(), pres.data(), its.data());
