@@ -169,6 +169,28 @@ def test_channelized_60x220_sources_both_precisions(bddc, pure_flux):
         assert np.abs(r2).max() <= 1e-10 * np.abs(u).max()
 
 
+@pytest.mark.parametrize("tau", [10.0, 100.0])
+def test_3d_subdomains_of_5_cubed_both_precisions(bddc, tau):
+    """Subdomains shaped like the 60 x 220 x 85 workload's (5^3 cells, up to
+    150 interface dofs: interior subdomains have six faces) on its 3D field
+    generator (ln k = 2.5 x Gaussian with channel layers at the bottom),
+    20 x 20 x 15 cells of 20 x 10 x 2 ft, 4 x 4 x 3 subdomains, adaptive
+    constraints (face averages alone leave kappa ~ 1.6e5 on this field)."""
+    from synth.problems import layered_3d
+    g = Grid(3, (20, 20, 15), (20.0, 10.0, 2.0))
+    t, v = pressure_drop_bc(g)
+    pb = Problem("c3-shaped", g, layered_3d(g, 1901), box_partition(g, (4, 4, 3)), t, v, np.zeros(g.n_cells))
+    o = BDDCOracle(pb, tau=tau)
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, tau, precision=bddc.BDDC_PREC_FP64)
+    assert st[0].n_subdomains == 48
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    flux32, pres32, its32, _, _ = gpu_solve(bddc, [pb], 1e-8, tau, precision=bddc.BDDC_PREC_FP32)
+    assert _rel(flux32, ref.flux) <= MIXED_REL and _rel(pres32, ref.pressure) <= MIXED_REL
+
+
 def test_operator_and_preconditioner_match_oracle(bddc):
     pb = make_config("c1")
     o = BDDCOracle(pb, tau=3.0)
