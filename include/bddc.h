@@ -66,6 +66,18 @@ extern "C" {
 #define BDDC_SCALING_MULTIPLICITY 0
 #define BDDC_SCALING_STIFFNESS 1
 
+/* Coarse solver (Algorithm 1, the coarse problem of Step 1 and of every
+ * preconditioner application).  Dense: the inverse of the coarse matrix,
+ * applied as one dense matrix-vector product (per instance n_c^2 doubles).
+ * Sparse: a multifrontal factorisation over a nested dissection of the
+ * subdomains, applied by forward and backward sweeps over the dissection
+ * tree.  Auto: dense while every instance has at most
+ * BDDC_COARSE_DENSE_MAX coarse dofs, sparse otherwise. */
+#define BDDC_COARSE_AUTO 0
+#define BDDC_COARSE_DENSE 1
+#define BDDC_COARSE_SPARSE 2
+#define BDDC_COARSE_DENSE_MAX 2048
+
 typedef struct {
     int dim;      /* 2 or 3 */
     int n[3];     /* cells per axis; n[2] == 1 in 2D */
@@ -93,6 +105,7 @@ typedef struct {
     int maxit;            /* CG iteration limit (> 0) */
     int pressure_scaling; /* 1: rescale the pressure block by D (Sec. 4) */
     int n_threads;        /* host threads used by setup; 0 = all cores */
+    int coarse_solver;    /* BDDC_COARSE_* */
 } bddc_options;
 
 typedef struct {
@@ -111,7 +124,8 @@ typedef struct {
 typedef struct bddc_handle bddc_handle;
 
 /* Default options: tau = 0 (face averages), multiplicity scaling, FP64,
- * maxit = 5000, pressure scaling on, all host threads. */
+ * maxit = 5000, pressure scaling on, all host threads, automatic coarse
+ * solver. */
 void bddc_default_options(bddc_options* opt);
 
 /* Set up one or more independent instances (Algorithm 1 setup: local
@@ -221,6 +235,10 @@ int bddc_last_solve_timing(const bddc_handle* h, double* kernel_ms, double* algo
  *   double: inst_vol inst_omega sub_d slot_w slot_dsig slot_coef slot_fcoefp g_bsign S F P Gpre
  *           Gpost Kinv P64  (F and P are FP64 copies of the operators the
  *           GPU applies, FP32-rounded for FP32 setups; P64 is the FP64 basis)
+ *   sparse coarse factor (empty with the dense coarse solver):
+ *   int32 : cn_inst cn_p cn_q cn_depth cn_dof cn_c0 cn_c1
+ *   int64 : inst_csoff inst_node0 cn_off_dof cn_off_X cn_off_H cn_off_u
+ *   double: cn_X cn_H cn_HT
  * bddc_host_setup_query gives the element count and size (0 count for an
  * unknown name); bddc_host_setup_copy copies the array into dst. */
 typedef struct bddc_host_setup bddc_host_setup;
@@ -234,6 +252,12 @@ int bddc_host_setup_create_gpu(int n_instances, const bddc_instance* inst, const
 int bddc_host_setup_query(const bddc_host_setup* hs, const char* name, int64_t* count, int* elem_bytes);
 int bddc_host_setup_copy(const bddc_host_setup* hs, const char* name, void* dst);
 void bddc_host_setup_destroy(bddc_host_setup* hs);
+/* x = K_c^{-1} rhs for one instance with the setup's coarse solver, on the
+ * host: the dense inverse, or the forward and backward sweeps over the
+ * packed multifrontal factor in the order the device runs them.  rhs and x
+ * are host arrays of n_c + N doubles (flux coarse dofs, then the subdomain
+ * pressures).  BDDC_E_INVALID_ARG for a null pointer or a bad instance. */
+int bddc_host_setup_coarse_solve(const bddc_host_setup* hs, int instance, const double* rhs, double* x);
 
 /* Diagnostic copy of a device work vector of the last solve into host
  * memory: "x" "r0" "r1" "d0" "d1" "g" "u0" (interface), "ql" "zl" "yl" "rl"

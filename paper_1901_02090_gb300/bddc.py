@@ -32,6 +32,10 @@ BDDC_PREC_FP64 = 0
 BDDC_PREC_FP32 = 1
 BDDC_SCALING_MULTIPLICITY = 0
 BDDC_SCALING_STIFFNESS = 1
+BDDC_COARSE_AUTO = 0
+BDDC_COARSE_DENSE = 1
+BDDC_COARSE_SPARSE = 2
+BDDC_COARSE_DENSE_MAX = 2048
 
 
 class bddc_grid(C.Structure):
@@ -45,7 +49,8 @@ class bddc_instance(C.Structure):
 
 class bddc_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("scaling", C.c_int), ("precision", C.c_int),
-                ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int)]
+                ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int),
+                ("coarse_solver", C.c_int)]
 
 
 class bddc_stats(C.Structure):
@@ -94,6 +99,7 @@ def _load():
         "bddc_host_setup_query": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
         "bddc_host_setup_destroy": (None, [P]),
+        "bddc_host_setup_coarse_solve": (C.c_int, [P, C.c_int, P, P]),
         "bddc_debug_vector": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_debug_phase_times": (C.c_int, [P, P, P]),
         "bddc_last_error": (C.c_char_p, [P]),
@@ -118,7 +124,8 @@ EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats"
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
             "bddc_subassembled_apply_noalloc",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_create_gpu", "bddc_host_setup_query",
-            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_debug_vector", "bddc_debug_phase_times",
+            "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_host_setup_coarse_solve",
+            "bddc_debug_vector", "bddc_debug_phase_times",
             "bddc_last_error",
             "bddc_error_string", "bddc_destroy",
             "bddc_server_create", "bddc_submit", "bddc_poll", "bddc_wait", "bddc_server_get_info",
@@ -306,7 +313,7 @@ class HostSetup:
     _INT64 = {"inst_goff", "inst_ng", "inst_coff", "inst_ncn", "inst_ncf", "inst_kinv_off", "inst_s0",
               "inst_s1", "inst_face_off", "inst_nfaces", "inst_cell_off", "inst_ncells", "off_S", "off_F",
               "off_P", "off_Gpre", "off_Gpost", "off_slot", "off_cslot", "off_cell", "off_int", "cell_gid",
-              "int_fid", "g_fid"}
+              "int_fid", "g_fid", "inst_csoff", "inst_node0", "cn_off_dof", "cn_off_X", "cn_off_H", "cn_off_u"}
 
     def get(self, name: str) -> np.ndarray:
         n, eb = C.c_int64(), C.c_int()
@@ -323,6 +330,15 @@ class HostSetup:
         if n.value:
             lib.bddc_host_setup_copy(self._h, name.encode(), out.ctypes.data)
         return out
+
+    def coarse_solve(self, instance: int, rhs) -> np.ndarray:
+        """K_c^{-1} rhs (n_c + N entries) with the setup's coarse solver, on the host."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.empty_like(rhs)
+        rc = lib.bddc_host_setup_coarse_solve(self._h, int(instance), rhs.ctypes.data, x.ctypes.data)
+        if rc != BDDC_OK:
+            raise BDDCError(rc, "bddc_host_setup_coarse_solve")
+        return x
 
     def close(self):
         if getattr(self, "_h", None):

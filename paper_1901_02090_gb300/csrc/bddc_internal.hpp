@@ -55,6 +55,22 @@ struct Packed {
     std::vector<double> g_bsign;  // +1 pressure face on a min side, -1 max side, 0 otherwise
     // per coarse flux dof (batched): the <= 2 coarse slots that hold it
     std::vector<int> c_slot_a, c_slot_b;
+    // sparse coarse factor (coarse_sparse = 1): per instance the offset of
+    // its coarse system vectors (n_cf + N + pure entries, inst_csoff) and of
+    // its nodes (inst_node0, n_inst + 1 entries); per node (batched): the
+    // instance, p, q, depth, offsets of its front dofs (P then B,
+    // instance-local) and of X (p x p), H (p x q) and HT (q x p); per front
+    // position the batched index, in the update array u, of the children's
+    // update for that dof (-1: none)
+    int coarse_sparse = 0;
+    std::vector<int64_t> inst_csoff, inst_node0;
+    std::vector<int> cn_inst, cn_p, cn_q, cn_depth;
+    std::vector<int64_t> cn_off_dof, cn_off_X, cn_off_H, cn_off_u;
+    std::vector<int> cn_dof;
+    std::vector<int> cn_c0, cn_c1;
+    std::vector<double> cn_X, cn_H, cn_HT;
+    int64_t n_csys = 0, n_cu = 0;
+    int cn_max_depth = 0;
     // matrices
     std::vector<double> S, F64, P64, Gpre, Gpost, Kinv;
     std::vector<float> F32, P32;
@@ -71,6 +87,27 @@ struct SetupResult {
     int code = BDDC_OK;
     std::string msg;
 };
+
+// The coarse problem in element form (one element per subdomain, over its
+// coarse dofs) and its multifrontal factor (bddc_coarse.cpp).
+struct CoarseElement {
+    std::vector<int> dofs;  // instance-local coarse dofs
+    std::vector<double> E;  // dofs.size()^2, row-major
+    double c[3] = {0.0, 0.0, 0.0};  // centroid of the subdomain
+};
+struct CoarseFactor {
+    int n = 0, root = -1, max_depth = 0;
+    // per node of the dissection tree, children before parents
+    std::vector<int> parent, child0, child1, depth;
+    std::vector<std::vector<int>> piv, bnd;   // the node's dofs P and its boundary B (sorted)
+    std::vector<std::vector<double>> X, H;    // X = F_PP^{-1} (p x p), H = X F_PB (p x q), row-major
+};
+// is_pressure[d]: d is a subdomain pressure (kept out of a node's pivots
+// once per node, see bddc_coarse.cpp)
+SetupResult factor_coarse(int n, const std::vector<CoarseElement>& el, const std::vector<char>& is_pressure,
+                          int leaf_max, int nthreads, CoarseFactor& f);
+// x = K^{-1} b with the factor (host; the device sweeps mirror it)
+void coarse_factor_solve(const CoarseFactor& f, const double* b, double* x);
 
 // Dense part of the local maps of a batch of subdomains (the interior saddle
 // solves behind S^i, G_pre and G_post, with iterative refinement), for the

@@ -811,6 +811,161 @@ __device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
 
 #include "bddc_mixed.cuh"
 
+// ---- sparse coarse solver: sweeps over the multifrontal factor ------------------------
+// (bddc_coarse.cpp builds the factor; this is its solve, FP64 on both paths)
+//
+// right-hand sides of every instance's coarse system (grid-stride over all
+// entries; a coarse problem has up to ~1e5 dofs): the flux part sums the
+// two coarse slots of each coarse flux dof, the pressure part is the Step-1
+// right-hand side (step1) or zero; the pure-flux multiplier row is zero
+template <class PR>
+__device__ void cs_rhs(const Params& p, bool step1) {
+    const int64_t total = p.inst_csoff[p.n_inst];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = p.n_inst - 1;  // the instance: last b with inst_csoff[b] <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.inst_csoff[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int b = lo;
+        const int64_t ncf = p.inst_ncf[b], ncn = p.inst_ncn[b], cfo = p.inst_cfoff[b], s0 = p.inst_s0[b];
+        const int64_t cs = p.inst_csoff[b], c = g - cs;
+        double v = 0.0;
+        if (c < ncf) {
+            const int a = p.c_slot_a[cfo + c], bb = p.c_slot_b[cfo + c];
+            if constexpr (PR::kMixed) {
+                const float2* rcl = reinterpret_cast<const float2*>(p.rcl);
+                v = (a >= 0 ? dd_dbl(__ldcg(rcl + a)) : 0.0) + (bb >= 0 ? dd_dbl(__ldcg(rcl + bb)) : 0.0);
+            } else {
+                v = (a >= 0 ? __ldcg(p.rcl + a) : 0.0) + (bb >= 0 ? __ldcg(p.rcl + bb) : 0.0);
+            }
+        } else if (c < ncn && step1) {
+            v = __ldcg(p.prhs + s0 + (c - ncf));
+        }
+        p.cs_b[g] = v;
+    }
+}
+
+// Both sweeps are GEMVs with the node's dense blocks; their dot products are
+// split into chunks of kCsChunk terms so that a level's work spreads over
+// many warps (the top fronts have ~1000 columns).  Each unit (node, block
+// of 32 outputs, chunk) stores its partial sums; the unit whose arrival
+// completes a block sums the partials in chunk order (independent of the
+// arrival order) and writes the block.  A block with one chunk writes
+// directly.
+constexpr int kCsChunk = 64;
+
+// the last of n arrivals at *cnt (whole warp; the completing warp resets it)
+__device__ __forceinline__ bool cs_arrive_last(int* cnt, int n) {
+    int last = 0;
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        last = arrive_acq_rel(cnt) == n - 1;
+        if (last) *cnt = 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) __threadfence();
+    return last != 0;
+}
+
+// forward unit (node v, block cb of 32 boundary rows, chunk ic of its
+// pivots): t_i = b_i + children's updates for the chunk's pivots (stored
+// for the backward sweep by the units of block 0), partial (H^T t)_j over
+// the chunk; the block's u_j = children's updates - sum of the partials
+__device__ void cs_forward(const Params& p, int4 un) {
+    const int l = threadIdx.x & 31;
+    const int v = un.x, cb = un.y, ic = un.z;
+    const int b = p.cn_inst[v], pp = p.cn_p[v], q = p.cn_q[v];
+    const int64_t od = p.cn_off_dof[v], oh = p.cn_off_H[v], ou = p.cn_off_u[v], cs = p.inst_csoff[b];
+    const int nic = pp > 0 ? (pp + kCsChunk - 1) / kCsChunk : 1;
+    const int j = cb * 32 + l;
+    const int i_lo = ic * kCsChunk, i_hi = (i_lo + kCsChunk < pp) ? i_lo + kCsChunk : pp;
+    double acc = 0.0;
+    for (int i0 = i_lo; i0 < i_hi; i0 += 32) {
+        double tl = 0.0;
+        if (i0 + l < i_hi) {
+            const int64_t fi = od + i0 + l;
+            const int d = p.cn_dof[fi], c0 = p.cn_c0[fi], c1 = p.cn_c1[fi];
+            tl = __ldcg(p.cs_b + cs + d) + (c0 >= 0 ? __ldcg(p.cs_u + c0) : 0.0) + (c1 >= 0 ? __ldcg(p.cs_u + c1) : 0.0);
+            if (cb == 0) p.cs_t[cs + d] = tl;
+        }
+        const int ni = (i_hi - i0 < 32) ? i_hi - i0 : 32;
+        const double* Hr = p.cn_H + oh + (int64_t)i0 * q + j;
+#pragma unroll 8
+        for (int k = 0; k < ni; ++k) {
+            const double tk = __shfl_sync(0xffffffffu, tl, k);
+            if (j < q) acc = fma(__ldg(Hr + (int64_t)k * q), tk, acc);
+        }
+    }
+    if (q == 0) return;
+    if (nic > 1) {
+        double* part = p.cs_fpart + p.cn_fwp_off[v] + ((int64_t)cb * nic + ic) * 32;
+        part[l] = acc;
+        if (!cs_arrive_last(p.cs_fcnt + p.cn_fwc_off[v] + cb, nic)) return;
+        part = p.cs_fpart + p.cn_fwp_off[v] + (int64_t)cb * nic * 32;
+        acc = 0.0;
+        for (int c = 0; c < nic; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
+    }
+    if (j < q) {
+        const int64_t fj = od + pp + j;
+        const int c0 = p.cn_c0[fj], c1 = p.cn_c1[fj];
+        p.cs_u[ou + j] = (c0 >= 0 ? __ldcg(p.cs_u + c0) : 0.0) + (c1 >= 0 ? __ldcg(p.cs_u + c1) : 0.0) - acc;
+    }
+}
+
+// backward unit (node v, block rb of 32 pivot rows, chunk kc of the
+// concatenated columns [P, B]): partial of x_i = sum_k X_ik t_k -
+// sum_j H_ij x_j (X symmetric: X_ik read as X[k][i]; H from its transpose);
+// the completed block goes to cs_x and, for the n_c + N coarse dofs, to wc
+template <class PR>
+__device__ void cs_backward(const Params& p, int4 un) {
+    const int l = threadIdx.x & 31;
+    const int v = un.x, rb = un.y, kc = un.z;
+    const int b = p.cn_inst[v], pp = p.cn_p[v], q = p.cn_q[v];
+    const int64_t od = p.cn_off_dof[v], ox = p.cn_off_X[v], oh = p.cn_off_H[v], cs = p.inst_csoff[b];
+    const int nkc = (pp + q + kCsChunk - 1) / kCsChunk;
+    const int i = rb * 32 + l;
+    const int k_lo = kc * kCsChunk, k_hi = (k_lo + kCsChunk < pp + q) ? k_lo + kCsChunk : pp + q;
+    double acc = 0.0;
+    for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
+        // the column values: t at pivots (k < p), x at boundary dofs (k >= p)
+        double vl = 0.0;
+        if (k0 + l < k_hi) {
+            const int kk = k0 + l;
+            const double* src = kk < pp ? p.cs_t : p.cs_x;
+            vl = __ldcg(src + cs + p.cn_dof[od + kk]);
+        }
+        const int nk = (k_hi - k0 < 32) ? k_hi - k0 : 32;
+#pragma unroll 8
+        for (int k = 0; k < nk; ++k) {
+            const double vk = __shfl_sync(0xffffffffu, vl, k);
+            const int kk = k0 + k;
+            if (i < pp) {
+                const double c = kk < pp ? __ldg(p.cn_X + ox + (int64_t)kk * pp + i)
+                                         : -__ldg(p.cn_HT + oh + (int64_t)(kk - pp) * pp + i);
+                acc = fma(c, vk, acc);
+            }
+        }
+    }
+    if (nkc > 1) {
+        double* part = p.cs_bpart + p.cn_bwp_off[v] + ((int64_t)rb * nkc + kc) * 32;
+        part[l] = acc;
+        if (!cs_arrive_last(p.cs_bcnt + p.cn_bwc_off[v] + rb, nkc)) return;
+        part = p.cs_bpart + p.cn_bwp_off[v] + (int64_t)rb * nkc * 32;
+        acc = 0.0;
+        for (int c = 0; c < nkc; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
+    }
+    if (i < pp) {
+        const int d = p.cn_dof[od + i];
+        p.cs_x[cs + d] = acc;
+        if (d < p.inst_ncn[b]) {
+            if constexpr (PR::kMixed) reinterpret_cast<float2*>(p.wc)[p.inst_coff[b] + d] = dd_of(acc);
+            else p.wc[p.inst_coff[b] + d] = acc;
+        }
+    }
+}
+
 // ---- the persistent solve kernel -------------------------------------------------------
 template <class PR>
 __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
@@ -836,14 +991,44 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
             else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
         }
     };
+    // a coarse solve and the grid barrier(s) after it: the dense inverse in
+    // one phase, or the sparse factor's right-hand side, forward sweep (tree
+    // depths deepest first) and backward sweep (root first), a phase each.
+    // Between the CG iterations, instances that are done skip their units.
+    auto coarse_solve = [&](bool step1, int id) -> bool {
+        if (!p.coarse_sparse) {
+            coarse_phase(step1);
+            return phase_end(p, id, nts);
+        }
+        cs_rhs<PR>(p, step1);
+        if (!phase_end(p, id, nts)) return false;
+        for (int d = p.cn_levels - 1; d >= 0; --d) {
+            const int64_t u0 = p.fw_off[d];
+            warp_range(p.fw_off[d + 1] - u0, a, e);
+            for (int64_t u = a; u < e; ++u) {
+                const int4 un = p.fw_unit[u0 + u];
+                if (step1 || !inst_done(p, p.cn_inst[un.x])) cs_forward(p, un);
+            }
+            if (!phase_end(p, id, nts)) return false;
+        }
+        for (int d = 0; d < p.cn_levels; ++d) {
+            const int64_t u0 = p.bw_off[d];
+            warp_range(p.bw_off[d + 1] - u0, a, e);
+            for (int64_t u = a; u < e; ++u) {
+                const int4 un = p.bw_unit[u0 + u];
+                if (step1 || !inst_done(p, p.cn_inst[un.x])) cs_backward<PR>(p, un);
+            }
+            if (!phase_end(p, id, nts)) return false;
+        }
+        return true;
+    };
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) {
         if constexpr (MX) mx_step1(p, s, w);
         else ph_step1<PR>(p, s, w);
     }
     if (!phase_end(p, 1, nts)) return;
-    coarse_phase(true);
-    if (!phase_end(p, 2, nts)) return;
+    if (!coarse_solve(true, 2)) return;
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) {
         if constexpr (MX) mx_u0(p, s, w);
@@ -857,8 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         else ph_fstar<PR>(p, s, w);
     }
     if (!phase_end(p, 5, nts)) return;
-    coarse_phase(false);
-    if (!phase_end(p, 6, nts)) return;
+    if (!coarse_solve(false, 6)) return;
     // each PROLONG ends with the convergence test of the next iteration
     warp_range(p.n_sub, a, e);
     for (int64_t s = a; s < e; ++s) {
@@ -879,8 +1063,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
             else ph_update<PR>(p, s, k, w);
         }
         if (!phase_end(p, 9, nts)) return;
-        coarse_phase(false);
-        if (!phase_end(p, 6, nts)) return;
+        if (!coarse_solve(false, 6)) return;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) {
             if constexpr (MX) mx_prolong(p, s, w, k + 1);
@@ -898,8 +1081,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         for (int64_t s = a; s < e; ++s)
             if (threadIdx.x == 0) p.prhs[s] = 0.0;
         if (!phase_end(p, 11, nts)) return;
-        coarse_phase(true);
-        if (!phase_end(p, 12, nts)) return;
+        if (!coarse_solve(true, 12)) return;
         warp_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s) mx_final_pressure(p, s);
         if (!phase_end(p, 13, nts)) return;
@@ -968,6 +1150,26 @@ __global__ void __launch_bounds__(kThreads) k_precond_coarse(Params p) {
     for (int64_t u = blockIdx.x; u < p.n_cunits; u += gridDim.x) {
         int staged = -1;
         ph_coarse<PR>(p, u, false, sm.rhs, staged);
+    }
+}
+
+// sparse coarse solve of the stand-alone preconditioner: right-hand sides,
+// then one launch per tree depth and sweep
+template <class PR>
+__global__ void __launch_bounds__(kThreads) k_cs_rhs(Params p) {
+    cs_rhs<PR>(p, false);
+}
+__global__ void __launch_bounds__(kThreads) k_cs_forward(Params p, int d) {
+    const int64_t W = (int64_t)gridDim.x * kWarps, u0 = p.fw_off[d], nu = p.fw_off[d + 1] - u0;
+    for (int64_t u = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); u < nu; u += W) {
+        cs_forward(p, p.fw_unit[u0 + u]);
+    }
+}
+template <class PR>
+__global__ void __launch_bounds__(kThreads) k_cs_backward(Params p, int d) {
+    const int64_t W = (int64_t)gridDim.x * kWarps, u0 = p.bw_off[d], nu = p.bw_off[d + 1] - u0;
+    for (int64_t u = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); u < nu; u += W) {
+        cs_backward<PR>(p, p.bw_unit[u0 + u]);
     }
 }
 
@@ -1047,6 +1249,7 @@ struct bddc_handle {
     InstState* pin_st = nullptr;            // pinned read-back of the per-instance state
     GridSync* pin_gs = nullptr;
     std::vector<int64_t> inst_cfoff;
+    std::vector<int64_t> fw_off_h, bw_off_h;  // sparse coarse: units per tree depth (host copies)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     float last_ms = 0.0f;
     double last_bytes = 0.0;
@@ -1060,13 +1263,16 @@ struct bddc_handle {
     mutable std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
 };
 
+// message of the last failed setup of this thread (bddc_last_error(NULL));
+// also set by the host-only setup in bddc_setup.cpp
+thread_local std::string g_setup_err;
+
 namespace {
 
 const char* kErrStrings[] = {"ok", "invalid argument", "invalid partition", "invalid permeability",
                              "out of memory", "not converged", "CG breakdown", "device wait timed out",
                              "CUDA error", "setup factorisation failed"};
 
-thread_local std::string g_setup_err;
 
 int set_err(bddc_handle* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -1119,6 +1325,7 @@ void bddc_default_options(bddc_options* opt) {
     opt->maxit = 5000;
     opt->pressure_scaling = 1;
     opt->n_threads = 0;
+    opt->coarse_solver = BDDC_COARSE_AUTO;
 }
 
 const char* bddc_error_string(int code) {
@@ -1149,7 +1356,8 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.maxit <= 0 || (opt.precision != BDDC_PREC_FP64 && opt.precision != BDDC_PREC_FP32) ||
-        (opt.scaling != BDDC_SCALING_MULTIPLICITY && opt.scaling != BDDC_SCALING_STIFFNESS))
+        (opt.scaling != BDDC_SCALING_MULTIPLICITY && opt.scaling != BDDC_SCALING_STIFFNESS) ||
+        opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE)
         return BDDC_E_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1239,6 +1447,49 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         if (!rc) rc = upload(h, cfp, &p.slot_fcoefp_f);
     }
     UP(inst_cfoff, h->inst_cfoff);
+    if (!rc && P.coarse_sparse) {
+        // multifrontal coarse factor and its work units per tree depth
+        p.coarse_sparse = 1;
+        UP(inst_csoff, P.inst_csoff); UP(cn_inst, P.cn_inst); UP(cn_p, P.cn_p); UP(cn_q, P.cn_q);
+        UP(cn_dof, P.cn_dof); UP(cn_c0, P.cn_c0); UP(cn_c1, P.cn_c1);
+        UP(cn_off_dof, P.cn_off_dof); UP(cn_off_X, P.cn_off_X); UP(cn_off_H, P.cn_off_H); UP(cn_off_u, P.cn_off_u);
+        UP(cn_X, P.cn_X); UP(cn_H, P.cn_H); UP(cn_HT, P.cn_HT);
+        const int L = P.cn_max_depth + 1;
+        const size_t nn = P.cn_p.size();
+        std::vector<std::vector<int4>> fw(L), bw(L);
+        std::vector<int64_t> fwc(nn), fwp(nn), bwc(nn), bwp(nn);
+        int64_t nfc = 0, nfp = 0, nbc = 0, nbp = 0;
+        for (size_t v = 0; v < nn; ++v) {
+            const int d = P.cn_depth[v], pp = P.cn_p[v], q = P.cn_q[v];
+            const int ncb = std::max(1, (q + 31) / 32), nic = pp > 0 ? (pp + kCsChunk - 1) / kCsChunk : 1;
+            const int nrb = (pp + 31) / 32, nkc = (pp + q + kCsChunk - 1) / kCsChunk;
+            for (int cb = 0; cb < ncb; ++cb)
+                for (int ic = 0; ic < nic; ++ic) fw[d].push_back(make_int4((int)v, cb, ic, 0));
+            for (int rb = 0; rb < nrb; ++rb)
+                for (int kc = 0; kc < nkc; ++kc) bw[d].push_back(make_int4((int)v, rb, kc, 0));
+            fwc[v] = nfc; nfc += ncb;
+            fwp[v] = nfp; nfp += (int64_t)ncb * nic * 32;
+            bwc[v] = nbc; nbc += nrb;
+            bwp[v] = nbp; nbp += (int64_t)nrb * nkc * 32;
+        }
+        UP(cn_fwc_off, fwc); UP(cn_fwp_off, fwp); UP(cn_bwc_off, bwc); UP(cn_bwp_off, bwp);
+        if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nfc, 1), &p.cs_fcnt);
+        if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nbc, 1), &p.cs_bcnt);
+        if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nfp, 1), &p.cs_fpart);
+        if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nbp, 1), &p.cs_bpart);
+        std::vector<int4> fu, bu;
+        std::vector<int64_t> fo(1, 0), bo(1, 0);
+        for (int d = 0; d < L; ++d) {
+            fu.insert(fu.end(), fw[d].begin(), fw[d].end());
+            bu.insert(bu.end(), bw[d].begin(), bw[d].end());
+            fo.push_back((int64_t)fu.size());
+            bo.push_back((int64_t)bu.size());
+        }
+        UP(fw_unit, fu); UP(bw_unit, bu); UP(fw_off, fo); UP(bw_off, bo);
+        h->fw_off_h = fo;
+        h->bw_off_h = bo;
+        p.cn_levels = L;
+    }
 #undef UP
     if (!rc) {
         if (opt.precision == BDDC_PREC_FP32) {
@@ -1305,6 +1556,9 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     AL(inst_cnt, (size_t)n_instances * kCounters); AL(inst_tot, (size_t)n_instances * kTotals);
     AL(st, n_instances); AL(alpha_hist, H); AL(beta_hist, H); AL(rho_hist, H);
     AL(n_active, 1); AL(gsync, 1);
+    if (P.coarse_sparse) {
+        AL(cs_b, P.n_csys); AL(cs_t, P.n_csys); AL(cs_x, P.n_csys); AL(cs_u, std::max<int64_t>(P.n_cu, 1));
+    }
     p.tstamp_cap = 16 + 4 * (opt.maxit + 2);
     AL(tstamp, 2 * (size_t)p.tstamp_cap);
 #undef AL
@@ -1318,7 +1572,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     p.maxit = opt.maxit;
     p.max_ng = std::max(P.max_ng, 1);
     p.max_in_post = std::max(P.max_in_post, 1);
-    p.max_ncn = std::max(P.max_ncn, 1);
+    p.max_ncn = P.coarse_sparse ? 2 : std::max(P.max_ncn, 1);  // the CTA rhs area of the dense coarse solve
     p.max_m = std::max(P.max_m, 1);
     h->smem = sizeof(double) * ((size_t)p.max_ncn +
                                 (size_t)kWarps * (2 * (size_t)p.max_ng + p.max_in_post + 2 * ((size_t)p.max_m + 1)));
@@ -1366,10 +1620,19 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         pre_b += 3.0 * fb * m * ng + 8.0 * ng * ng + fb * ng * ng + 8.0 * 20.0 * ng;
         post_b += 8.0 * ng * (ni + nc) + 8.0 * (ni + 2.0 * nc + 2.0 * ng);
     }
-    for (int b = 0; b < n_instances; ++b) {
-        const double ncn = P.inst_ncn[b], ncf = P.inst_ncf[b];
-        it_b += 8.0 * ncn * ncf;
-        pre_b += 8.0 * ncn * ncn + 8.0 * ncn * ncf;
+    if (P.coarse_sparse) {
+        // a sparse coarse solve reads X, H (forward) and H^T (backward) once
+        double cb = 0.0;
+        for (size_t v = 0; v < P.cn_p.size(); ++v)
+            cb += 8.0 * ((double)P.cn_p[v] * P.cn_p[v] + 2.0 * P.cn_p[v] * P.cn_q[v]);
+        it_b += cb;
+        pre_b += 2.0 * cb;
+    } else {
+        for (int b = 0; b < n_instances; ++b) {
+            const double ncn = P.inst_ncn[b], ncf = P.inst_ncf[b];
+            it_b += 8.0 * ncn * ncf;
+            pre_b += 8.0 * ncn * ncn + 8.0 * ncn * ncf;
+        }
     }
     h->bytes_iter = it_b;
     h->bytes_pre = pre_b;
@@ -1596,13 +1859,34 @@ int bddc_apply_preconditioner(bddc_handle* h, const double* r, double* z, double
     cudaMemsetAsync(p.st, 0, sizeof(InstState) * h->n_inst, h->stream);
     const int grid = (int)std::min<int64_t>((p.n_sub + kWarps - 1) / kWarps, 4096);
     const int cgrid = (int)std::min<int64_t>(p.n_cunits, 4096);
+    // the stand-alone kernels keep the coarse vectors in FP64 on both paths,
+    // so the sparse sweeps run in their FP64 instantiation
+    auto coarse = [&](bool mixed) {
+        if (p.coarse_sparse) {
+            const int igrid = (int)std::min<int64_t>((h->P.n_csys + kThreads - 1) / kThreads, 4096);
+            k_cs_rhs<PrecFP64><<<igrid, kThreads, 0, h->stream>>>(p);
+            for (int d = p.cn_levels - 1; d >= 0; --d) {
+                const int64_t nu = h->fw_off_h[d + 1] - h->fw_off_h[d];
+                if (nu > 0) k_cs_forward<<<(int)std::min<int64_t>((nu + kWarps - 1) / kWarps, 4096), kThreads, 0, h->stream>>>(p, d);
+            }
+            for (int d = 0; d < p.cn_levels; ++d) {
+                const int64_t nu = h->bw_off_h[d + 1] - h->bw_off_h[d];
+                if (nu > 0)
+                    k_cs_backward<PrecFP64><<<(int)std::min<int64_t>((nu + kWarps - 1) / kWarps, 4096), kThreads, 0, h->stream>>>(p, d);
+            }
+        } else if (mixed) {
+            k_precond_coarse<PrecMixed><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        } else {
+            k_precond_coarse<PrecFP64><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        }
+    };
     if (h->precision == BDDC_PREC_FP32) {
         k_precond_restrict<PrecMixed><<<grid, kThreads, h->smem, h->stream>>>(p, r);
-        k_precond_coarse<PrecMixed><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        coarse(true);
         k_precond_prolong<PrecMixed><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
     } else {
         k_precond_restrict<PrecFP64><<<grid, kThreads, h->smem, h->stream>>>(p, r);
-        k_precond_coarse<PrecFP64><<<cgrid, kThreads, h->smem, h->stream>>>(p);
+        coarse(false);
         k_precond_prolong<PrecFP64><<<grid, kThreads, h->smem, h->stream>>>(p, z0);
     }
     const int64_t L = h->P.off_slot.back();

@@ -93,6 +93,26 @@ struct Params {
     double *alpha_hist, *beta_hist, *rho_hist;                 // n_inst x (maxit + 1)
     int* n_active;
     GridSync* gsync;
+    // sparse coarse solver (coarse_sparse = 1, bddc_coarse.cpp): per node of
+    // every instance's dissection tree p, q, the offsets of its front dofs
+    // (P then B, instance-local), of X (p x p, symmetric), H (p x q), HT
+    // (q x p) and of its update vector in cs_u; per front position the cs_u
+    // index of each child's update for that dof (-1: none).  Work units per
+    // tree depth: forward (blocks of 32 B rows of H^T t) and backward (blocks
+    // of 32 P rows of x), each split into chunks of its dot products, with
+    // prefix offsets per depth.
+    int coarse_sparse, cn_levels;
+    const int64_t* inst_csoff;
+    const int *cn_inst, *cn_p, *cn_q, *cn_dof, *cn_c0, *cn_c1;
+    const int64_t *cn_off_dof, *cn_off_X, *cn_off_H, *cn_off_u;
+    const double *cn_X, *cn_H, *cn_HT;
+    double *cs_b, *cs_t, *cs_x, *cs_u;
+    const int64_t *fw_off, *bw_off;
+    const int4 *fw_unit, *bw_unit;  // (node, block of 32 outputs, chunk of the dot products, -)
+    // per node: offsets of its blocks' arrival counters and partial sums
+    const int64_t *cn_fwc_off, *cn_fwp_off, *cn_bwc_off, *cn_bwp_off;
+    int *cs_fcnt, *cs_bcnt;
+    double *cs_fpart, *cs_bpart;
     // phase timestamps (CTA 0 at each barrier): pairs (phase id, ns)
     long long* tstamp;
     int tstamp_cap;

@@ -123,7 +123,8 @@ struct Inst {
     std::vector<Face> faces;
     int n_cf = 0, n_adapt = 0;
     bool pure = false;
-    std::vector<double> Kinv;       // (n_cf + N) square
+    std::vector<double> Kinv;       // (n_cf + N) square (dense coarse solver)
+    CoarseFactor cf;                // multifrontal coarse factor (sparse coarse solver)
     double omega = 0.0;
 };
 
@@ -898,13 +899,23 @@ double adaptive_face(const Inst& I, const Face& F, double tau, std::vector<std::
     return omega;
 }
 
-SetupResult coarse(Inst& I) {
+// The coarse problem (Sec. 3, eqs. (two-level_coarse-1/2)) in element form:
+// per subdomain its coarse dofs (local coarse rows, its pressure, and the
+// global-mean multiplier of a pure-flux problem) and the element matrix
+// [Psi^T S Psi, d sigma^T Psi; ., 0] (plus d |Omega_i| to the multiplier).
+std::vector<CoarseElement> coarse_elements(const Inst& I) {
     const int ncf = I.n_cf, N = I.N;
     const int n = ncf + N + (I.pure ? 1 : 0);
-    std::vector<double> K((size_t)n * n, 0.0);
+    std::vector<CoarseElement> el(N);
     for (int s = 0; s < N; ++s) {
         const Sub& S = I.subs[s];
         const int ng = S.ng, m = S.m;
+        const int e = m + 1 + (I.pure ? 1 : 0);
+        CoarseElement& E = el[s];
+        E.dofs.assign(S.cid.begin(), S.cid.begin() + m);
+        E.dofs.push_back(ncf + s);
+        if (I.pure) E.dofs.push_back(n - 1);
+        E.E.assign((size_t)e * e, 0.0);
         // Psi^T S Psi and b(psi, 1_s) = d_s sigma^T Psi
         std::vector<double> SP((size_t)m * ng, 0.0);   // (S Psi)^T
         for (int a = 0; a < m; ++a)
@@ -917,19 +928,40 @@ SetupResult coarse(Inst& I) {
             for (int b = 0; b < m; ++b) {
                 double v = 0.0;
                 for (int i = 0; i < ng; ++i) v += S.PsiT[(size_t)a * ng + i] * SP[(size_t)b * ng + i];
-                K[(size_t)S.cid[a] * n + S.cid[b]] += v;
+                E.E[(size_t)a * e + b] = v;
             }
             double bv = 0.0;
             for (int i = 0; i < ng; ++i) bv += S.sigma[i] * S.PsiT[(size_t)a * ng + i];
             bv *= S.d;
-            K[(size_t)(ncf + s) * n + S.cid[a]] += bv;
-            K[(size_t)S.cid[a] * n + (ncf + s)] += bv;
+            E.E[(size_t)m * e + a] = bv;
+            E.E[(size_t)a * e + m] = bv;
         }
         if (I.pure) {
             const double v = S.d * S.nc * I.geo.vol;
-            K[(size_t)(ncf + s) * n + (n - 1)] = v;
-            K[(size_t)(n - 1) * n + (ncf + s)] = v;
+            E.E[(size_t)m * e + m + 1] = v;
+            E.E[(size_t)(m + 1) * e + m] = v;
         }
+        // centroid (nested dissection of the sparse coarse factor)
+        for (int64_t c : S.cells) {
+            const int64_t i = c % I.geo.nx, j = (c / I.geo.nx) % I.geo.ny, k = c / ((int64_t)I.geo.nx * I.geo.ny);
+            E.c[0] += (i + 0.5) * I.geo.h[0];
+            E.c[1] += (j + 0.5) * I.geo.h[1];
+            E.c[2] += (k + 0.5) * I.geo.h[2];
+        }
+        for (int a = 0; a < 3; ++a) E.c[a] /= (double)std::max<size_t>(1, S.cells.size());
+    }
+    return el;
+}
+
+// dense coarse solver: the inverse of the assembled coarse matrix
+SetupResult coarse_dense(Inst& I, const std::vector<CoarseElement>& el) {
+    const int ncf = I.n_cf, N = I.N;
+    const int n = ncf + N + (I.pure ? 1 : 0);
+    std::vector<double> K((size_t)n * n, 0.0);
+    for (const CoarseElement& E : el) {
+        const int e = (int)E.dofs.size();
+        for (int a = 0; a < e; ++a)
+            for (int b = 0; b < e; ++b) K[(size_t)E.dofs[a] * n + E.dofs[b]] += E.E[(size_t)a * e + b];
     }
     std::vector<int> piv;
     if (!lu(n, K.data(), piv)) return {BDDC_E_SETUP, "singular coarse problem"};
@@ -943,6 +975,18 @@ SetupResult coarse(Inst& I) {
     for (double v : I.Kinv)
         if (!std::isfinite(v)) return {BDDC_E_SETUP, "non-finite coarse inverse"};
     return {};
+}
+
+// subdomains per leaf of the coarse dissection tree
+constexpr int kCoarseLeafSubdomains = 8;
+
+SetupResult coarse(Inst& I, bool sparse, int nthreads) {
+    const std::vector<CoarseElement> el = coarse_elements(I);
+    if (!sparse) return coarse_dense(I, el);
+    const int n = I.n_cf + I.N + (I.pure ? 1 : 0);
+    std::vector<char> is_pressure(n, 0);
+    for (int s = 0; s < I.N; ++s) is_pressure[I.n_cf + s] = 1;
+    return factor_coarse(n, el, is_pressure, kCoarseLeafSubdomains, nthreads, I.cf);
 }
 
 }  // namespace
@@ -1107,8 +1151,17 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         if (r.code) fail(r, b, s);
     });
     if (err.code) return err;
+    // coarse solver: dense inverse, or the sparse factor for large coarse problems
+    int max_ncn = 0;
+    for (int b = 0; b < n_inst; ++b) max_ncn = std::max(max_ncn, I[b].n_cf + I[b].N);
+    const bool sparse = opt.coarse_solver == BDDC_COARSE_SPARSE ||
+                        (opt.coarse_solver == BDDC_COARSE_AUTO && max_ncn > BDDC_COARSE_DENSE_MAX);
     std::vector<SetupResult> cres(n_inst);
-    parallel_for(n_inst, nthreads, [&](int64_t b) { cres[b] = coarse(I[b]); });
+    if (sparse) {
+        for (int b = 0; b < n_inst; ++b) cres[b] = coarse(I[b], true, nthreads);
+    } else {
+        parallel_for(n_inst, nthreads, [&](int64_t b) { cres[b] = coarse(I[b], false, 1); });
+    }
     for (int b = 0; b < n_inst; ++b)
         if (cres[b].code) { cres[b].msg = "instance " + std::to_string(b) + ": " + cres[b].msg; return cres[b]; }
 
@@ -1224,7 +1277,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         }
         for (int64_t q = 0; q < ngam; ++q) { P.g_slot_a.push_back(sa[q]); P.g_slot_b.push_back(sb[q]); }
         for (int c = 0; c < In.n_cf; ++c) { P.c_slot_a.push_back(ca[c]); P.c_slot_b.push_back(cb[c]); }
-        goff += ngam; coff += ncn; kinv_off += (int64_t)ncn * ncn; s_glob += In.N;
+        goff += ngam; coff += ncn; kinv_off += (int64_t)In.Kinv.size(); s_glob += In.N;
         face_off += In.geo.n_faces; cell_off += In.geo.n_cells;
     }
     // slot partner (the other copy of the same interface dof)
@@ -1237,6 +1290,58 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     P.n_sub = s_glob;
     P.n_gamma = goff;
     P.n_coarse_vec = coff;
+    if (sparse) {
+        // the multifrontal factors of all instances, batched
+        P.coarse_sparse = 1;
+        int64_t csoff = 0, u_off = 0, dof_off = 0, xo = 0, ho = 0;
+        for (int b = 0; b < n_inst; ++b) {
+            const CoarseFactor& cf = I[b].cf;
+            const int nn = (int)cf.piv.size();
+            P.inst_csoff.push_back(csoff);
+            P.inst_node0.push_back((int64_t)P.cn_p.size());
+            std::vector<int64_t> uo(nn);
+            for (int v = 0; v < nn; ++v) {
+                uo[v] = u_off;
+                u_off += (int64_t)cf.bnd[v].size();
+            }
+            auto child_pos = [&](int c, int d) -> int {
+                if (c < 0) return -1;
+                const std::vector<int>& cb = cf.bnd[c];
+                const auto it = std::lower_bound(cb.begin(), cb.end(), d);
+                return (it != cb.end() && *it == d) ? (int)(uo[c] + (it - cb.begin())) : -1;
+            };
+            for (int v = 0; v < nn; ++v) {
+                const int p = (int)cf.piv[v].size(), q = (int)cf.bnd[v].size();
+                P.cn_inst.push_back(b);
+                P.cn_p.push_back(p);
+                P.cn_q.push_back(q);
+                P.cn_depth.push_back(cf.depth[v]);
+                P.cn_off_dof.push_back(dof_off);
+                P.cn_off_X.push_back(xo);
+                P.cn_off_H.push_back(ho);
+                P.cn_off_u.push_back(uo[v]);
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int d : pass ? cf.bnd[v] : cf.piv[v]) {
+                        P.cn_dof.push_back(d);
+                        P.cn_c0.push_back(child_pos(cf.child0[v], d));
+                        P.cn_c1.push_back(child_pos(cf.child1[v], d));
+                    }
+                P.cn_X.insert(P.cn_X.end(), cf.X[v].begin(), cf.X[v].end());
+                P.cn_H.insert(P.cn_H.end(), cf.H[v].begin(), cf.H[v].end());
+                for (int j = 0; j < q; ++j)
+                    for (int i = 0; i < p; ++i) P.cn_HT.push_back(cf.H[v][(size_t)i * q + j]);
+                dof_off += p + q;
+                xo += (int64_t)p * p;
+                ho += (int64_t)p * q;
+            }
+            P.cn_max_depth = std::max(P.cn_max_depth, cf.max_depth);
+            csoff += cf.n;
+        }
+        P.inst_csoff.push_back(csoff);
+        P.inst_node0.push_back((int64_t)P.cn_p.size());
+        P.n_csys = csoff;
+        P.n_cu = u_off;
+    }
     return {};
 }
 
@@ -1246,6 +1351,9 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
 struct bddc_host_setup {
     bddc::Packed P;
 };
+
+// message of the last failed setup of this thread (bddc_last_error(NULL))
+extern thread_local std::string g_setup_err;
 
 namespace {
 template <class T>
@@ -1270,6 +1378,8 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
     E(inst_face_off); E(inst_nfaces); E(inst_cell_off); E(inst_ncells); E(off_S); E(off_F); E(off_P);
     E(off_Gpre); E(off_Gpost); E(off_slot); E(off_cslot); E(off_cell); E(off_int); E(cell_gid); E(int_fid); E(g_fid);
     E(inst_vol); E(inst_omega); E(sub_d); E(slot_w); E(slot_dsig); E(g_bsign); E(S); E(Gpre); E(Gpost); E(Kinv); E(P64);
+    E(inst_csoff); E(inst_node0); E(cn_inst); E(cn_p); E(cn_q); E(cn_depth); E(cn_off_dof); E(cn_off_X); E(cn_off_H);
+    E(cn_off_u); E(cn_dof); E(cn_c0); E(cn_c1); E(cn_X); E(cn_H); E(cn_HT);
 #undef E
     if (n == "F" || n == "P") {
         const bool isF = n == "F";
@@ -1288,9 +1398,59 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
     if (eb) *eb = 0;
     return false;
 }
+// x = K_c^{-1} rhs for instance b with the packed coarse solver (dense
+// inverse, or the multifrontal sweeps over the packed factor exactly as the
+// device runs them); rhs and x have n_c + N entries
+void packed_coarse_solve(const bddc::Packed& P, int b, const double* rhs, double* x) {
+    const int64_t ncn = P.inst_ncn[b];
+    if (!P.coarse_sparse) {
+        const double* K = P.Kinv.data() + P.inst_kinv_off[b];
+        for (int64_t r = 0; r < ncn; ++r) {
+            double acc = 0.0;
+            for (int64_t c = 0; c < ncn; ++c) acc += K[r * ncn + c] * rhs[c];
+            x[r] = acc;
+        }
+        return;
+    }
+    const int64_t n = P.inst_csoff[b + 1] - P.inst_csoff[b];
+    std::vector<double> bb(n, 0.0), t(n, 0.0), xx(n, 0.0), u(P.n_cu, 0.0);
+    for (int64_t c = 0; c < ncn; ++c) bb[c] = rhs[c];
+    const int64_t v0 = P.inst_node0[b], v1 = P.inst_node0[b + 1];
+    auto upd = [&](int c) { return c >= 0 ? u[c] : 0.0; };
+    for (int64_t v = v0; v < v1; ++v) {
+        const int p = P.cn_p[v], q = P.cn_q[v];
+        const int64_t od = P.cn_off_dof[v], oh = P.cn_off_H[v], ou = P.cn_off_u[v];
+        for (int i = 0; i < p; ++i) {
+            const int d = P.cn_dof[od + i];
+            t[d] = bb[d] + upd(P.cn_c0[od + i]) + upd(P.cn_c1[od + i]);
+        }
+        for (int j = 0; j < q; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < p; ++i) acc += P.cn_H[oh + (int64_t)i * q + j] * t[P.cn_dof[od + i]];
+            u[ou + j] = upd(P.cn_c0[od + p + j]) + upd(P.cn_c1[od + p + j]) - acc;
+        }
+    }
+    for (int64_t v = v1 - 1; v >= v0; --v) {
+        const int p = P.cn_p[v], q = P.cn_q[v];
+        const int64_t od = P.cn_off_dof[v], ox = P.cn_off_X[v], oh = P.cn_off_H[v];
+        for (int i = 0; i < p; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < p; ++k) acc += P.cn_X[ox + (int64_t)k * p + i] * t[P.cn_dof[od + k]];
+            for (int j = 0; j < q; ++j) acc -= P.cn_HT[oh + (int64_t)j * p + i] * xx[P.cn_dof[od + p + j]];
+            xx[P.cn_dof[od + i]] = acc;
+        }
+    }
+    for (int64_t c = 0; c < ncn; ++c) x[c] = xx[c];
+}
 }  // namespace
 
 extern "C" {
+
+int bddc_host_setup_coarse_solve(const bddc_host_setup* hs, int instance, const double* rhs, double* x) {
+    if (!hs || !rhs || !x || instance < 0 || instance >= (int)hs->P.inst_ncn.size()) return BDDC_E_INVALID_ARG;
+    packed_coarse_solve(hs->P, instance, rhs, x);
+    return BDDC_OK;
+}
 
 static int host_setup_create(int n_instances, const bddc_instance* inst, const bddc_options* opt_in,
                              bddc_host_setup** out, bddc::LocalMapsDevice device) {
@@ -1300,9 +1460,11 @@ static int host_setup_create(int n_instances, const bddc_instance* inst, const b
     bddc_options opt;
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
+    if (opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE) return BDDC_E_INVALID_ARG;
     auto* hs = new bddc_host_setup();
     bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P, device);
     if (r.code) {
+        g_setup_err = r.msg;
         delete hs;
         return r.code;
     }

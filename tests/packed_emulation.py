@@ -23,6 +23,10 @@ class Packed:
                      "inst_vol", "sub_d", "slot_w", "slot_dsig", "g_bsign", "S", "F", "P", "Gpre",
                      "Gpost", "Kinv", "slot_fcs", "cslot_n", "slot_coef", "P64"):
             setattr(self, name, hs.get(name))
+        # sparse coarse solver: no dense inverse; coarse solves go through
+        # the host sweeps over the packed multifrontal factor
+        self.coarse_sparse = len(hs.get("cn_p")) > 0
+        self.hs = hs
         self.n_sub = len(self.sub_ng)
         self.n_inst = len(self.inst_ng)
         self.G = int(self.inst_ng.sum())
@@ -114,13 +118,16 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000, mixed=False):
         wc = []
         for b in range(P.n_inst):
             ncn, ncf = int(P.inst_ncn[b]), int(P.inst_ncf[b])
-            K = P.Kinv[P.inst_kinv_off[b]:P.inst_kinv_off[b] + ncn * ncn].reshape(ncn, ncn)
             rhs = np.zeros(ncn)
             for s in range(P.inst_s0[b], P.inst_s1[b]):
                 np.add.at(rhs, cid[s], rc_parts[s])
             if prhs is not None:
                 rhs[ncf:] = prhs[P.inst_s0[b]:P.inst_s1[b]]
-            wc.append(K @ rhs)
+            if P.coarse_sparse:
+                wc.append(P.hs.coarse_solve(b, rhs))
+            else:
+                K = P.Kinv[P.inst_kinv_off[b]:P.inst_kinv_off[b] + ncn * ncn].reshape(ncn, ncn)
+                wc.append(K @ rhs)
         return wc
 
     g = P.g_bsign * np.where(P.g_bsign != 0, bc[P.g_fid], 0.0)
