@@ -90,9 +90,9 @@ enum : int { kCtrRR = 0, kCtrRZ = 1, kCtrDQ = 2, kCounters = 3 };
 enum : int { kTotRR = 0, kTotRZ = 1, kTotDQ = 2, kTotA1 = 3, kTotA2 = 4, kTotals = 5 };
 constexpr double kRhoFluxConverged = 1e-24;
 
-__device__ __forceinline__ int arrive_acq_rel(int* cnt) {
+__device__ __forceinline__ int arrive_acq_rel(int* cnt, int n = 1) {
     int old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(cnt), "r"(n) : "memory");
     return old;
 }
 
@@ -171,15 +171,17 @@ __device__ void cg_alpha(const Params& p, int b, int k, double dq) {
     }
 }
 
-// count this warp's partial of kind ctr (stored by lane 0 before the call);
-// the completing warp publishes the total and takes the scalar step
-__device__ void publish_total(const Params& p, int64_t s, int ctr, int k = 0, bool with_a = false,
+// count the arrival of n subdomains of instance b whose partials of kind
+// ctr this warp has stored; the completing warp publishes the total and
+// takes the scalar step.  A warp counts all its consecutive subdomains of
+// an instance with one atomic (it usually holds several per phase).
+__device__ void publish_total(const Params& p, int b, int n, int ctr, int k = 0, bool with_a = false,
                               bool fp64_correction = false) {
-    const int b = p.sub_inst[s];
     const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
     int* cnt = p.inst_cnt + (int64_t)b * kCounters + ctr;
     int last = 0;
-    if ((threadIdx.x & 31) == 0) last = arrive_acq_rel(cnt) == (int)(s1 - s0) - 1;
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) last = arrive_acq_rel(cnt, n) == (int)(s1 - s0) - n;
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
@@ -637,15 +639,17 @@ __device__ void ph_fstar(const Params& p, int64_t s, WarpSm& w) {
         p.dp1[s] = 0.0;
     }
     __syncwarp();
-    publish_total(p, s, kCtrRR, true);
+    publish_total(p, p.sub_inst[s], 1, kCtrRR, 0, true);
     restrict_apply<PR>(p, s, w);
 }
 
+// The CG phases store their partials and return false for an instance that
+// is done; the caller counts the arrivals (publish_total).
 template <class PR>
-__device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
+__device__ bool ph_prolong(const Params& p, int64_t s, WarpSm& w) {
     using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s];
     const double* wcb = p.wc + p.inst_coff[b];
@@ -671,15 +675,15 @@ __device__ void ph_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
         p.zp[s] = __ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]);
     }
     __syncwarp();
-    publish_total(p, s, kCtrRZ, k_next, false, !PR::kMixed);
+    return true;
 }
 
 // direction update d = z + beta d and operator apply q = S d + B_0^T d_p
 template <class PR>
-__device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     using S_t = typename PR::S_t;
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
     const double beta = __ldcg(p.beta_hist + (int64_t)b * (p.maxit + 1) + k);
     double* dold = (k & 1) ? p.dbuf0 : p.dbuf1;
@@ -710,13 +714,13 @@ __device__ void ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     dq = warp_sum(dq);
     if (l == 0) p.part_dq[s] = dq;
     __syncwarp();
-    publish_total(p, s, kCtrDQ, k);
+    return true;
 }
 
 template <class PR>
-__device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
     const double alpha = __ldcg(p.alpha_hist + (int64_t)b * (p.maxit + 1) + k);
     const double* rold = (k & 1) ? p.rbuf1 : p.rbuf0;
@@ -746,8 +750,8 @@ __device__ void ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
         p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
     }
     __syncwarp();
-    publish_total(p, s, kCtrRR);
     restrict_apply<PR>(p, s, w);
+    return true;
 }
 
 // mixed path: FP64 restriction of the final residual for the closing coarse
@@ -1043,32 +1047,43 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     }
     if (!phase_end(p, 5, nts)) return;
     if (!coarse_solve(false, 6)) return;
+    // a CG phase over the warp's subdomains; the arrivals of its consecutive
+    // subdomains of one instance are counted at once (publish_total)
+    auto cg_phase = [&](int ctr, int kk, auto&& unit) {
+        warp_range(p.n_sub, a, e);
+        int cur = -1, n = 0;
+        for (int64_t s = a; s < e; ++s) {
+            const int b = p.sub_inst[s];
+            if (b != cur) {
+                if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
+                cur = b;
+                n = 0;
+            }
+            if (unit(s)) ++n;
+        }
+        if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
+    };
     // each PROLONG ends with the convergence test of the next iteration
-    warp_range(p.n_sub, a, e);
-    for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_prolong(p, s, w, 0);
-        else ph_prolong<PR>(p, s, w, 0);
-    }
+    auto prolong_unit = [&](int64_t s) -> bool {
+        if constexpr (MX) return mx_prolong(p, s, w);
+        else return ph_prolong<PR>(p, s, w);
+    };
+    cg_phase(kCtrRZ, 0, prolong_unit);
     if (!phase_end(p, 7, nts)) return;
     for (int k = 0;; ++k) {
         if (__ldcg(p.n_active) <= 0) break;
-        warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_dirop(p, s, k, w);
-            else ph_dirop<PR>(p, s, k, w);
-        }
+        cg_phase(kCtrDQ, k, [&](int64_t s) -> bool {
+            if constexpr (MX) return mx_dirop(p, s, k, w);
+            else return ph_dirop<PR>(p, s, k, w);
+        });
         if (!phase_end(p, 8, nts)) return;
-        for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_update(p, s, k, w);
-            else ph_update<PR>(p, s, k, w);
-        }
+        cg_phase(kCtrRR, k, [&](int64_t s) -> bool {
+            if constexpr (MX) return mx_update(p, s, k, w);
+            else return ph_update<PR>(p, s, k, w);
+        });
         if (!phase_end(p, 9, nts)) return;
         if (!coarse_solve(false, 6)) return;
-        warp_range(p.n_sub, a, e);
-        for (int64_t s = a; s < e; ++s) {
-            if constexpr (MX) mx_prolong(p, s, w, k + 1);
-            else ph_prolong<PR>(p, s, w, k + 1);
-        }
+        cg_phase(kCtrRZ, k + 1, prolong_unit);
         if (!phase_end(p, 7, nts)) return;
     }
     if constexpr (MX) {

@@ -264,13 +264,13 @@ __device__ void mx_fstar(const Params& p, int64_t s, WarpSm& w) {
         p.dp1[s] = 0.0;
     }
     __syncwarp();
-    publish_total(p, s, kCtrRR, true);
+    publish_total(p, p.sub_inst[s], 1, kCtrRR, 0, true);
     mx_restrict(p, s, w);
 }
 
-__device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
+__device__ bool mx_prolong(const Params& p, int64_t s, WarpSm& w) {
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
     const float2* wcb = V2(p.wc) + p.inst_coff[b];
@@ -291,13 +291,13 @@ __device__ void mx_prolong(const Params& p, int64_t s, WarpSm& w, int k_next) {
         p.zp[s] = dd_dbl(__ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]));
     }
     __syncwarp();
-    publish_total(p, s, kCtrRZ, k_next);
+    return true;
 }
 
 // direction update and operator apply (pairs)
-__device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
     const double beta = __ldcg(p.beta_hist + (int64_t)b * (p.maxit + 1) + k);
     const float2 beta2 = dd_of(beta);
@@ -333,12 +333,12 @@ __device__ void mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     dq = dd_warp_sum(dq);
     if (l == 0) p.part_dq[s] = dd_dbl(dq);
     __syncwarp();
-    publish_total(p, s, kCtrDQ, k);
+    return true;
 }
 
-__device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
-    if (inst_done(p, b)) return;
+    if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
     const double alpha = __ldcg(p.alpha_hist + (int64_t)b * (p.maxit + 1) + k);
     const float2 alpha2 = dd_of(alpha);
@@ -374,8 +374,8 @@ __device__ void mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
         p.xp[s] = __ldcg(p.xp + s) + alpha * __ldcg(dpcur + s);
     }
     __syncwarp();
-    publish_total(p, s, kCtrRR);
     mx_restrict(p, s, w);
+    return true;
 }
 
 // closing FP64 coarse pressure correction: FP64 restriction of the final

@@ -6,7 +6,8 @@ the same sweeps; and the 3D configuration at full size (60x220x85 cells,
 8976 subdomains of 5^3 cells), whose coarse problem only the sparse solver
 holds, converges to a solution that is cellwise conservative and satisfies
 the flux equation on sampled faces (checked with the oracle's cell
-matrices)."""
+matrices); so does the same grid under the seeded irregular box partition
+(boxes of 3-8 cells per axis, 7568 subdomains of 27-512 cells)."""
 
 import time
 
@@ -135,11 +136,13 @@ def _flux_equation_residual_sample(disc, flux, pres, n_sample, seed):
     return np.array(res), np.array(scale)
 
 
-def test_config3_full_size_converges_conservative(bddc):
-    """60x220x85 cells (1.12M cells, 3.4M faces), 12x44x17 subdomains of 5^3,
-    layered 3D field with channelized lower third, adaptive tau = 10, mixed
-    path: the automatic coarse solver picks the sparse factor."""
-    pb = make_config("c3")
+@pytest.mark.parametrize("name,n_sub", [("c3", 8976), ("c4", 7568)])
+def test_3d_full_size_converges_conservative(bddc, name, n_sub):
+    """60x220x85 cells (1.12M cells, 3.4M faces), 12x44x17 subdomains of 5^3
+    (c3) or irregular boxes of 3-8 cells per axis (c4), layered 3D field with
+    channelized lower third, adaptive tau = 10, mixed path: the automatic
+    coarse solver picks the sparse factor."""
+    pb = make_config(name)
     opt = bddc.default_options(tau=10.0, precision=bddc.BDDC_PREC_FP32)
     t0 = time.time()
     h = bddc.setup([pb], opt, stream=torch.cuda.current_stream().cuda_stream)
@@ -151,10 +154,10 @@ def test_config3_full_size_converges_conservative(bddc):
     st = h.stats(0)
     ms, _ = h.last_solve_timing()
     h.close()
-    print(f"config 3: setup {t_setup:.1f} s, solve {ms:.1f} ms, {int(its[0])} iterations, "
+    print(f"{name}: setup {t_setup:.1f} s, solve {ms:.1f} ms, {int(its[0])} iterations, "
           f"n_coarse {st.n_coarse}, adaptive {st.n_adaptive}, kappa {st.kappa:.2f}")
     assert rc == bddc.BDDC_OK and st.status == bddc.BDDC_OK
-    assert st.n_subdomains == 8976 and st.n_coarse > bddc.BDDC_COARSE_DENSE_MAX
+    assert st.n_subdomains == n_sub and st.n_coarse > bddc.BDDC_COARSE_DENSE_MAX
     assert st.relres <= 1e-8
     assert np.all(np.isfinite(flux)) and np.all(np.isfinite(pres))
     disc = Discretization(pb)
