@@ -56,6 +56,7 @@ struct Params {
     const double* inst_vol;
     // subdomains
     int64_t n_sub;
+    const int64_t* warp_sub0;  // per warp of the solve launch: first subdomain of its range (warps + 1)
     const int *sub_inst, *sub_ng, *sub_ni, *sub_nc, *sub_m, *sub_local;
     const int64_t *off_S, *off_F, *off_P, *off_Gpre, *off_Gpost, *off_slot, *off_cslot, *off_cell, *off_int;
     const double* sub_d;
