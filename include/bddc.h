@@ -119,6 +119,9 @@ typedef struct {
     int n_interface;       /* interface flux dofs (incl. pressure faces) */
     int n_coarse;          /* coarse dofs: flux constraints + N pressures */
     int n_adaptive;        /* adaptive constraints added by Algorithm 3 */
+    double true_relres;    /* ||r|| / ||rhs|| of the full RT0/P0 saddle system (Sec. 2) at the
+                              returned flux and pressure: both block rows, every free face and
+                              cell, applied matrix-free on the GPU after the solve */
 } bddc_stats;
 
 typedef struct bddc_handle bddc_handle;

@@ -56,7 +56,8 @@ class bddc_options(C.Structure):
 class bddc_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("kappa", C.c_double),
                 ("relres", C.c_double), ("omega_tilde", C.c_double), ("n_subdomains", C.c_int),
-                ("n_interface", C.c_int), ("n_coarse", C.c_int), ("n_adaptive", C.c_int)]
+                ("n_interface", C.c_int), ("n_coarse", C.c_int), ("n_adaptive", C.c_int),
+                ("true_relres", C.c_double)]
 
 
 class bddc_request_info(C.Structure):

@@ -71,6 +71,13 @@ struct Packed {
     std::vector<double> cn_X, cn_H, cn_HT;
     int64_t n_csys = 0, n_cu = 0;
     int cn_max_depth = 0;
+    // the full-space system of every instance, for the true residual of a
+    // solution (the RT0/P0 saddle system of Sec. 2 applied matrix-free):
+    // per instance dim, nx, ny, nz and the cell size; per cell 1/k per axis
+    // (stride 3); per face its boundary type
+    std::vector<int> inst_grid;
+    std::vector<double> inst_h, cell_kinv;
+    std::vector<int8_t> face_bct;
     // matrices
     std::vector<double> S, F64, P64, Gpre, Gpost, Kinv;
     std::vector<float> F32, P32;

@@ -1223,6 +1223,118 @@ __global__ void __launch_bounds__(kThreads) k_precond_prolong(Params p, double* 
     }
 }
 
+// ---- true residual of the full saddle system (matrix-free RT0/P0) -----------------
+// For the solution (u, p) of instance b, the residuals of both block rows of
+// the discrete system of Sec. 2 (eqs. (a), (b), (rhs); the pressure faces
+// carry g = +-p_N on the min / max side): on every free face e
+//   r_e = g_e - sum over its two cells c of (a_c u)_e - (B^T p)_e,
+// with the exact RT0 cell block (h_a^2 / |c|) k_a^-1 [1/3 1/6; 1/6 1/3] on
+// the two a-faces of a cell and B(c, lower face) = +1, B(c, upper face) = -1;
+// on every cell  r_c = -f_c |c| - (B u)_c.  CTA (b, chunk) covers a chunk of
+// instance b's faces and cells and writes its sums of r_e^2, g_e^2, r_c^2
+// and (f_c |c|)^2; k_true_residual_sum adds the chunks in order (a fixed
+// summation order: bitwise reproducible) and writes
+// sqrt(sum r^2) / sqrt(sum rhs^2) per instance.
+constexpr int kTrChunks = 16;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) t += sh[w];
+    return t;  // valid on thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) k_true_residual(Params p) {
+    __shared__ double sh[kWarps];
+    const int b = blockIdx.x / kTrChunks, chunk = blockIdx.x % kTrChunks;
+    const int dim = p.inst_grid[4 * b], nx = p.inst_grid[4 * b + 1], ny = p.inst_grid[4 * b + 2],
+              nz = p.inst_grid[4 * b + 3];
+    const double* h = p.inst_h + 3 * b;
+    const double vol = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
+    const int64_t f0 = p.inst_face_off[b], c0 = p.inst_cell_off[b];
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    int64_t cnt[3];
+    cnt[0] = (int64_t)(nx + 1) * ny * nz;
+    cnt[1] = (int64_t)nx * (ny + 1) * nz;
+    cnt[2] = dim == 3 ? (int64_t)nx * ny * (nz + 1) : 0;
+    const int64_t nface = cnt[0] + cnt[1] + cnt[2];
+    const double* u = p.flux_out + f0;
+    const double* pr = p.p_out + c0;
+    double r1 = 0.0, g2 = 0.0, r2 = 0.0, f2 = 0.0;
+    const int64_t fa = nface * chunk / kTrChunks, fb = nface * (chunk + 1) / kTrChunks;
+    for (int64_t e = fa + threadIdx.x; e < fb; e += kThreads) {
+        const int bt = p.face_bct[f0 + e];
+        if (bt == 0) continue;  // no-flow face: not an unknown
+        int a = 0;
+        int64_t r = e;
+        while (r >= cnt[a]) r -= cnt[a++];
+        const int64_t ex = nx + (a == 0), ey = ny + (a == 1);
+        const int64_t i = r % ex, j = (r / ex) % ey, k = r / (ex * ey);
+        const int64_t pos = a == 0 ? i : (a == 1 ? j : k), na = a == 0 ? nx : (a == 1 ? ny : nz);
+        const int64_t step = a == 0 ? 1 : (a == 1 ? ex : ex * ey);  // face id step along axis a
+        const int64_t cstep = a == 0 ? 1 : (a == 1 ? nx : (int64_t)nx * ny);  // cell id step along axis a
+        const double s = h[a] * h[a] / vol;
+        double au = 0.0, btp = 0.0;
+        const double ue = u[e];
+        // the cell above the face along a has the face's indices; the one below is a step back
+        const int64_t ci = i + (int64_t)nx * (j + (int64_t)ny * k);
+        if (pos < na) {  // e is the lower a-face of the cell above
+            const int64_t c = ci;
+            au += s * p.cell_kinv[3 * (c0 + c) + a] * (ue / 3.0 + u[e + step] / 6.0);
+            btp += pr[c];
+        }
+        if (pos > 0) {  // e is the upper a-face of the cell below
+            const int64_t c = ci - cstep;
+            au += s * p.cell_kinv[3 * (c0 + c) + a] * (u[e - step] / 6.0 + ue / 3.0);
+            btp -= pr[c];
+        }
+        const double g = bt == 1 ? (pos == 0 ? p.bc_in[f0 + e] : -p.bc_in[f0 + e]) : 0.0;
+        const double res = g - au - btp;
+        r1 += res * res;
+        g2 += g * g;
+    }
+    const int64_t ca = ncell * chunk / kTrChunks, cb = ncell * (chunk + 1) / kTrChunks;
+    for (int64_t c = ca + threadIdx.x; c < cb; c += kThreads) {
+        const int64_t i = c % nx, j = (c / nx) % ny, k = c / ((int64_t)nx * ny);
+        double div = 0.0;
+        for (int a = 0; a < dim; ++a) {
+            const int64_t ex = nx + (a == 0), ey = ny + (a == 1);
+            int64_t off = 0;
+            for (int q = 0; q < a; ++q) off += cnt[q];
+            const int64_t lo = off + i + ex * (j + ey * k);
+            const int64_t step = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
+            div += u[lo] - u[lo + step];
+        }
+        const double rhs = -p.f_in[c0 + c] * vol;
+        const double res = rhs - div;
+        r2 += res * res;
+        f2 += rhs * rhs;
+    }
+    double* out = p.tr_part + 4 * (int64_t)blockIdx.x;
+    const double s1 = block_sum(r1, sh);
+    if (threadIdx.x == 0) out[0] = s1;
+    const double s2 = block_sum(g2, sh);
+    if (threadIdx.x == 0) out[1] = s2;
+    const double s3 = block_sum(r2, sh);
+    if (threadIdx.x == 0) out[2] = s3;
+    const double s4 = block_sum(f2, sh);
+    if (threadIdx.x == 0) out[3] = s4;
+}
+
+__global__ void k_true_residual_sum(Params p) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.n_inst) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < kTrChunks; ++c)
+        for (int q = 0; q < 4; ++q) s[q] += p.tr_part[4 * ((int64_t)b * kTrChunks + c) + q];
+    const double den = s[1] + s[3];
+    p.tr_out[b] = sqrt(s[0] + s[2]) / (den > 0.0 ? sqrt(den) : 1.0);
+}
+
 // FP64 -> FP32 pair (hi, lo) elementwise, on the device
 __global__ void k_pairs(int64_t n, const double* src, float2* dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1271,6 +1383,7 @@ struct bddc_handle {
     mutable std::vector<bddc_stats> stats;  // kappa filled on demand (bddc_get_stats)
     mutable bool kappa_stale = false;       // the last solve's kappa is not computed yet
     InstState* pin_st = nullptr;            // pinned read-back of the per-instance state
+    double* pin_tr = nullptr;               // pinned read-back of the true residuals
     GridSync* pin_gs = nullptr;
     std::vector<int64_t> inst_cfoff;
     std::vector<int64_t> fw_off_h, bw_off_h;  // sparse coarse: units per tree depth (host copies)
@@ -1364,6 +1477,7 @@ void bddc_destroy(bddc_handle* h) {
     if (!h) return;
     for (void* p : h->allocs) cudaFree(p);
     if (h->pin_st) cudaFreeHost(h->pin_st);
+    if (h->pin_tr) cudaFreeHost(h->pin_tr);
     if (h->pin_gs) cudaFreeHost(h->pin_gs);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -1471,6 +1585,8 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         if (!rc) rc = upload(h, cfp, &p.slot_fcoefp_f);
     }
     UP(inst_cfoff, h->inst_cfoff);
+    UP(inst_grid, P.inst_grid); UP(inst_h, P.inst_h); UP(cell_kinv, P.cell_kinv); UP(face_bct, P.face_bct);
+    UP(inst_face_off, P.inst_face_off); UP(inst_cell_off, P.inst_cell_off);
     if (!rc && P.coarse_sparse) {
         // multifrontal coarse factor and its work units per tree depth
         p.coarse_sparse = 1;
@@ -1580,6 +1696,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     AL(inst_cnt, (size_t)n_instances * kCounters); AL(inst_tot, (size_t)n_instances * kTotals);
     AL(st, n_instances); AL(alpha_hist, H); AL(beta_hist, H); AL(rho_hist, H);
     AL(n_active, 1); AL(gsync, 1);
+    AL(tr_part, (size_t)n_instances * kTrChunks * 4); AL(tr_out, n_instances);
     if (P.coarse_sparse) {
         AL(cs_b, P.n_csys); AL(cs_t, P.n_csys); AL(cs_x, P.n_csys); AL(cs_u, std::max<int64_t>(P.n_cu, 1));
     }
@@ -1645,6 +1762,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     cudaEventCreate(&h->ev0);
     cudaEventCreate(&h->ev1);
     if (cudaMallocHost((void**)&h->pin_st, sizeof(InstState) * n_instances) != cudaSuccess ||
+        cudaMallocHost((void**)&h->pin_tr, sizeof(double) * n_instances) != cudaSuccess ||
         cudaMallocHost((void**)&h->pin_gs, sizeof(GridSync)) != cudaSuccess) {
         bddc_destroy(h);
         return BDDC_E_OOM;
@@ -1749,6 +1867,10 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(h->grid), dim3(kThreads), args, h->smem, st);
     cudaEventRecord(h->ev1, st);
     if (e != cudaSuccess) return set_err(h, BDDC_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    // the true residual of the full system at the solution
+    k_true_residual<<<h->n_inst * kTrChunks, kThreads, 0, st>>>(p);
+    k_true_residual_sum<<<(h->n_inst + 127) / 128, 128, 0, st>>>(p);
+    cudaMemcpyAsync(h->pin_tr, p.tr_out, sizeof(double) * h->n_inst, cudaMemcpyDeviceToHost, st);
     if (!flux_dev) cudaMemcpyAsync(flux, p.flux_out, nface * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (!p_dev) cudaMemcpyAsync(pressure, p.p_out, ncell * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(h->pin_st, p.st, sizeof(InstState) * h->n_inst, cudaMemcpyDeviceToHost, st);
@@ -1768,6 +1890,7 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
         S.iterations = hs[b].iterations;
         S.status = hs[b].done ? hs[b].status : BDDC_E_TIMEOUT;
         S.relres = hs[b].relres;
+        S.true_relres = h->pin_tr[b];
         const int m = S.iterations;
         S.kappa = 0.0;  // computed on demand from the CG coefficients
         its_h[b] = S.iterations;

@@ -120,6 +120,15 @@ struct Params {
     // io
     const double *f_in, *bc_in;
     double *flux_out, *p_out;
+    // the full-space system (true residual of the solution): per instance
+    // dim, nx, ny, nz, the cell size, face and cell offsets; per cell 1/k per
+    // axis (stride 3); per face its boundary type (-1 inside, 0 no flow, 1
+    // pressure); per (instance, chunk) CTA four partial sums
+    const int* inst_grid;
+    const double *inst_h, *cell_kinv;
+    const int64_t *inst_face_off, *inst_cell_off;
+    const int8_t* face_bct;
+    double *tr_part, *tr_out;
     // control
     int maxit;
     double tol;

@@ -1186,6 +1186,11 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         P.inst_vol.push_back(In.geo.vol);
         P.inst_nadapt.push_back(In.n_adapt);
         P.inst_omega.push_back(In.omega);
+        P.inst_grid.insert(P.inst_grid.end(), {In.geo.dim, In.geo.nx, In.geo.ny, In.geo.nz});
+        P.inst_h.insert(P.inst_h.end(), {In.geo.h[0], In.geo.h[1], In.geo.h[2]});
+        for (int64_t c = 0; c < In.geo.n_cells; ++c)
+            for (int a = 0; a < 3; ++a) P.cell_kinv.push_back(a < In.geo.dim ? In.kinv[(size_t)c * In.geo.dim + a] : 0.0);
+        P.face_bct.insert(P.face_bct.end(), In.bct.begin(), In.bct.end());
         P.max_ncn = std::max(P.max_ncn, ncn);
         P.Kinv.insert(P.Kinv.end(), In.Kinv.begin(), In.Kinv.end());
         // per interface dof

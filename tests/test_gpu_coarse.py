@@ -155,10 +155,11 @@ def test_3d_full_size_converges_conservative(bddc, name, n_sub):
     ms, _ = h.last_solve_timing()
     h.close()
     print(f"{name}: setup {t_setup:.1f} s, solve {ms:.1f} ms, {int(its[0])} iterations, "
-          f"n_coarse {st.n_coarse}, adaptive {st.n_adaptive}, kappa {st.kappa:.2f}")
+          f"n_coarse {st.n_coarse}, adaptive {st.n_adaptive}, kappa {st.kappa:.2f}, true relres {st.true_relres:.2e}")
     assert rc == bddc.BDDC_OK and st.status == bddc.BDDC_OK
     assert st.n_subdomains == n_sub and st.n_coarse > bddc.BDDC_COARSE_DENSE_MAX
     assert st.relres <= 1e-8
+    assert st.true_relres <= 1e-6  # the full saddle system at the returned solution (GPU, matrix-free)
     assert np.all(np.isfinite(flux)) and np.all(np.isfinite(pres))
     disc = Discretization(pb)
     cf = disc.cell_faces
