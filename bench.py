@@ -367,6 +367,7 @@ def main():
     iters = [h.stats(i).iterations for i in range(B)]
     kappas = [h.stats(i).kappa for i in range(B)]
     n_adapt = [h.stats(i).n_adaptive for i in range(B)]
+    true_res = [h.stats(i).true_relres for i in range(B)]
     total_ms = max_over_ranks(total_ms, world)
     value = whole_job_value(world, B, K, total_ms)
 
@@ -409,6 +410,8 @@ def main():
                    "setup_s": round(setup_s, 2)},
         "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
         "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
+        # ||r|| / ||rhs|| of the full RT0/P0 system at each returned solution (GPU, after the solve)
+        "true_relres_max": float(np.max(true_res)),
         "fp64_single": fp64_single,
         "serving": serving,
         "latency_batched_ms": {"p50": float(np.percentile(kms, 50)), "p99": float(np.percentile(kms, 99)),
