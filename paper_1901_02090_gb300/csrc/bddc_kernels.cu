@@ -1251,63 +1251,68 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 __global__ void __launch_bounds__(kThreads) k_true_residual(Params p) {
     __shared__ double sh[kWarps];
     const int b = blockIdx.x / kTrChunks, chunk = blockIdx.x % kTrChunks;
+    // 32-bit index arithmetic: an instance has < 2^31 faces
     const int dim = p.inst_grid[4 * b], nx = p.inst_grid[4 * b + 1], ny = p.inst_grid[4 * b + 2],
               nz = p.inst_grid[4 * b + 3];
     const double* h = p.inst_h + 3 * b;
     const double vol = h[0] * h[1] * (dim == 3 ? h[2] : 1.0);
     const int64_t f0 = p.inst_face_off[b], c0 = p.inst_cell_off[b];
-    const int64_t ncell = (int64_t)nx * ny * nz;
-    int64_t cnt[3];
-    cnt[0] = (int64_t)(nx + 1) * ny * nz;
-    cnt[1] = (int64_t)nx * (ny + 1) * nz;
-    cnt[2] = dim == 3 ? (int64_t)nx * ny * (nz + 1) : 0;
-    const int64_t nface = cnt[0] + cnt[1] + cnt[2];
     const double* u = p.flux_out + f0;
     const double* pr = p.p_out + c0;
+    const int8_t* bct = p.face_bct + f0;
+    const double* bcv = p.bc_in + f0;
+    const double* kinv = p.cell_kinv + 3 * c0;
     double r1 = 0.0, g2 = 0.0, r2 = 0.0, f2 = 0.0;
-    const int64_t fa = nface * chunk / kTrChunks, fb = nface * (chunk + 1) / kTrChunks;
-    for (int64_t e = fa + threadIdx.x; e < fb; e += kThreads) {
-        const int bt = p.face_bct[f0 + e];
-        if (bt == 0) continue;  // no-flow face: not an unknown
-        int a = 0;
-        int64_t r = e;
-        while (r >= cnt[a]) r -= cnt[a++];
-        const int64_t ex = nx + (a == 0), ey = ny + (a == 1);
-        const int64_t i = r % ex, j = (r / ex) % ey, k = r / (ex * ey);
-        const int64_t pos = a == 0 ? i : (a == 1 ? j : k), na = a == 0 ? nx : (a == 1 ? ny : nz);
-        const int64_t step = a == 0 ? 1 : (a == 1 ? ex : ex * ey);  // face id step along axis a
-        const int64_t cstep = a == 0 ? 1 : (a == 1 ? nx : (int64_t)nx * ny);  // cell id step along axis a
+    int off = 0;  // first face of axis a
+    for (int a = 0; a < dim; ++a) {
+        const unsigned ex = nx + (a == 0), ey = ny + (a == 1), ez = nz + (a == 2 && dim == 3);
+        const unsigned cnt = ex * ey * ez;
+        const unsigned na = a == 0 ? nx : (a == 1 ? ny : nz);
+        const unsigned step = a == 0 ? 1u : (a == 1 ? ex : ex * ey);                    // face id step along a
+        const unsigned cstep = a == 0 ? 1u : (a == 1 ? (unsigned)nx : (unsigned)nx * ny);  // cell id step along a
         const double s = h[a] * h[a] / vol;
-        double au = 0.0, btp = 0.0;
-        const double ue = u[e];
-        // the cell above the face along a has the face's indices; the one below is a step back
-        const int64_t ci = i + (int64_t)nx * (j + (int64_t)ny * k);
-        if (pos < na) {  // e is the lower a-face of the cell above
-            const int64_t c = ci;
-            au += s * p.cell_kinv[3 * (c0 + c) + a] * (ue / 3.0 + u[e + step] / 6.0);
-            btp += pr[c];
+        const unsigned fa = (unsigned)((uint64_t)cnt * chunk / kTrChunks), fb = (unsigned)((uint64_t)cnt * (chunk + 1) / kTrChunks);
+        for (unsigned r = fa + threadIdx.x; r < fb; r += kThreads) {
+            const int e = off + (int)r;
+            const int bt = bct[e];
+            if (bt == 0) continue;  // no-flow face: not an unknown
+            const unsigned i = r % ex, jk = r / ex, j = jk % ey, k = jk / ey;
+            const unsigned pos = a == 0 ? i : (a == 1 ? j : k);
+            // the cell above the face along a has the face's indices; the one below is a step back
+            const unsigned ci = i + (unsigned)nx * (j + (unsigned)ny * k);
+            const double ue = u[e];
+            double au = 0.0, btp = 0.0;
+            // the RT0 cell block entries 1/3 and 1/6 as products: FP64 division
+            // is a long instruction sequence at GB300's FP64 rate
+            constexpr double kThird = 1.0 / 3.0, kSixth = 1.0 / 6.0;
+            if (pos < na) {  // e is the lower a-face of the cell above
+                au += s * kinv[3 * ci + a] * (kThird * ue + kSixth * u[e + step]);
+                btp += pr[ci];
+            }
+            if (pos > 0) {  // e is the upper a-face of the cell below
+                const unsigned c = ci - cstep;
+                au += s * kinv[3 * c + a] * (kSixth * u[e - step] + kThird * ue);
+                btp -= pr[c];
+            }
+            const double g = bt == 1 ? (pos == 0 ? bcv[e] : -bcv[e]) : 0.0;
+            const double res = g - au - btp;
+            r1 += res * res;
+            g2 += g * g;
         }
-        if (pos > 0) {  // e is the upper a-face of the cell below
-            const int64_t c = ci - cstep;
-            au += s * p.cell_kinv[3 * (c0 + c) + a] * (u[e - step] / 6.0 + ue / 3.0);
-            btp -= pr[c];
-        }
-        const double g = bt == 1 ? (pos == 0 ? p.bc_in[f0 + e] : -p.bc_in[f0 + e]) : 0.0;
-        const double res = g - au - btp;
-        r1 += res * res;
-        g2 += g * g;
+        off += (int)cnt;
     }
-    const int64_t ca = ncell * chunk / kTrChunks, cb = ncell * (chunk + 1) / kTrChunks;
-    for (int64_t c = ca + threadIdx.x; c < cb; c += kThreads) {
-        const int64_t i = c % nx, j = (c / nx) % ny, k = c / ((int64_t)nx * ny);
-        double div = 0.0;
-        for (int a = 0; a < dim; ++a) {
-            const int64_t ex = nx + (a == 0), ey = ny + (a == 1);
-            int64_t off = 0;
-            for (int q = 0; q < a; ++q) off += cnt[q];
-            const int64_t lo = off + i + ex * (j + ey * k);
-            const int64_t step = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
-            div += u[lo] - u[lo + step];
+    // cells: per axis the lower face is at (i, j, k) of the axis' face grid
+    const unsigned ncell = (unsigned)nx * ny * nz;
+    const unsigned ca = (unsigned)((uint64_t)ncell * chunk / kTrChunks), cb = (unsigned)((uint64_t)ncell * (chunk + 1) / kTrChunks);
+    const unsigned fo1 = (unsigned)(nx + 1) * ny * nz, fo2 = fo1 + (unsigned)nx * (ny + 1) * nz;
+    for (unsigned c = ca + threadIdx.x; c < cb; c += kThreads) {
+        const unsigned i = c % nx, jk = c / nx, j = jk % ny, k = jk / ny;
+        const unsigned lx = i + (nx + 1) * (j + (unsigned)ny * k);
+        const unsigned ly = fo1 + i + (unsigned)nx * (j + (unsigned)(ny + 1) * k);
+        double div = (u[lx] - u[lx + 1]) + (u[ly] - u[ly + nx]);
+        if (dim == 3) {
+            const unsigned lz = fo2 + i + (unsigned)nx * (j + (unsigned)ny * k);
+            div += u[lz] - u[lz + (unsigned)nx * ny];
         }
         const double rhs = -p.f_in[c0 + c] * vol;
         const double res = rhs - div;
