@@ -278,6 +278,15 @@ int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64
  * *count receives the number of int64 entries; pairs may be NULL. */
 int bddc_debug_phase_times(const bddc_handle* h, int64_t* pairs, int64_t* count);
 
+/* Failure-detection diagnostic of the bounded grid-barrier wait: launches
+ * n_ctas (2..1024) CTAs that enter one grid barrier except the last, which
+ * never arrives; the others give up after limit_ns (0 < limit <= 60 s) and
+ * set the error flag.  Returns BDDC_E_TIMEOUT when the wait ran out as
+ * designed (the device context stays usable), BDDC_OK if it did not,
+ * BDDC_E_INVALID_ARG or BDDC_E_CUDA.  The solve kernel's barriers use the
+ * same wait with a 10 s limit. */
+int bddc_debug_barrier_timeout(long long limit_ns, int n_ctas);
+
 const char* bddc_last_error(const bddc_handle* h);
 const char* bddc_error_string(int code);
 void bddc_destroy(bddc_handle* h);

@@ -101,6 +101,7 @@ def _load():
         "bddc_host_setup_copy": (C.c_int, [P, C.c_char_p, P]),
         "bddc_host_setup_destroy": (None, [P]),
         "bddc_host_setup_coarse_solve": (C.c_int, [P, C.c_int, P, P]),
+        "bddc_debug_barrier_timeout": (C.c_int, [C.c_longlong, C.c_int]),
         "bddc_debug_vector": (C.c_int, [P, C.c_char_p, P, P]),
         "bddc_debug_phase_times": (C.c_int, [P, P, P]),
         "bddc_last_error": (C.c_char_p, [P]),
@@ -126,7 +127,7 @@ EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats"
             "bddc_subassembled_apply_noalloc",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_create_gpu", "bddc_host_setup_query",
             "bddc_host_setup_copy", "bddc_host_setup_destroy", "bddc_host_setup_coarse_solve",
-            "bddc_debug_vector", "bddc_debug_phase_times",
+            "bddc_debug_vector", "bddc_debug_phase_times", "bddc_debug_barrier_timeout",
             "bddc_last_error",
             "bddc_error_string", "bddc_destroy",
             "bddc_server_create", "bddc_submit", "bddc_poll", "bddc_wait", "bddc_server_get_info",

@@ -206,8 +206,11 @@ __device__ void publish_total(const Params& p, int b, int n, int ctr, int k = 0,
     else if (ctr == kCtrDQ) cg_alpha(p, b, k, v);
 }
 
-// grid-wide barrier with a bounded wait; false if any CTA gave up
-__device__ bool grid_barrier(GridSync* gs) {
+// grid-wide barrier with a wait bounded in time (limit_ns of %globaltimer);
+// past the limit the CTA sets the error flag and returns false, as does
+// every CTA that finds the flag set, so the kernel ends and the host reads
+// BDDC_E_TIMEOUT with the context intact
+__device__ bool grid_barrier(GridSync* gs, long long limit_ns = kBarrierWaitNs) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -221,10 +224,15 @@ __device__ bool grid_barrier(GridSync* gs) {
             __threadfence();
             atomicAdd(&gs->gen, 1u);
         } else {
-            long long spins = 0;
-            while (*vgen == g0) {
-                if (++spins > kSpinLimit) { ok = 0; break; }
+            long long t0, t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (unsigned int spins = 1; *vgen == g0; ++spins) {
                 __nanosleep(32);
+                if ((spins & 255) == 0) {
+                    if (*(volatile int*)&gs->error) { ok = 0; break; }
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > limit_ns) { ok = 0; break; }
+                }
             }
         }
         __threadfence();
@@ -1340,6 +1348,13 @@ __global__ void k_true_residual_sum(Params p) {
     p.tr_out[b] = sqrt(s[0] + s[2]) / (den > 0.0 ? sqrt(den) : 1.0);
 }
 
+// diagnostic of the bounded barrier wait: the last CTA never arrives, so
+// the others give up after limit_ns and set the error flag
+__global__ void k_barrier_probe(GridSync* gs, long long limit_ns) {
+    if (blockIdx.x == gridDim.x - 1) return;
+    grid_barrier(gs, limit_ns);
+}
+
 // FP64 -> FP32 pair (hi, lo) elementwise, on the device
 __global__ void k_pairs(int64_t n, const double* src, float2* dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1999,6 +2014,22 @@ int bddc_debug_phase_times(const bddc_handle* h, int64_t* pairs, int64_t* count)
     if (pairs && cudaMemcpy(pairs, h->prm.tstamp, n * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
         return BDDC_E_CUDA;
     return BDDC_OK;
+}
+
+int bddc_debug_barrier_timeout(long long limit_ns, int n_ctas) {
+    if (limit_ns <= 0 || limit_ns > 60000000000LL || n_ctas < 2 || n_ctas > 1024) return BDDC_E_INVALID_ARG;
+    GridSync* gs = nullptr;
+    if (cudaMalloc((void**)&gs, sizeof(GridSync)) != cudaSuccess) {
+        cudaGetLastError();
+        return BDDC_E_CUDA;
+    }
+    cudaMemset(gs, 0, sizeof(GridSync));
+    k_barrier_probe<<<n_ctas, 32>>>(gs, limit_ns);
+    GridSync hgs{};
+    const cudaError_t e = cudaMemcpy(&hgs, gs, sizeof(GridSync), cudaMemcpyDeviceToHost);
+    cudaFree(gs);
+    if (e != cudaSuccess) return BDDC_E_CUDA;
+    return hgs.error ? BDDC_E_TIMEOUT : BDDC_OK;
 }
 
 int bddc_get_stats(const bddc_handle* h, int instance, bddc_stats* out) {

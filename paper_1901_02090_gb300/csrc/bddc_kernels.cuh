@@ -30,7 +30,7 @@ namespace bddc {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCoarseRows = 16;             // coarse rows per work unit
-constexpr long long kSpinLimit = 1LL << 24; // grid-barrier spins before giving up
+constexpr long long kBarrierWaitNs = 10000000000LL;  // a grid-barrier wait past 10 s is an error
 
 struct GridSync {
     unsigned int count;
