@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbddc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["bddc_kernels.cu", "bddc_setup.cpp", "bddc_server.cpp", "bddc_setup_gpu.cu", "bddc_coarse.cpp"]
+SOURCES = ["bddc_kernels.cu", "bddc_setup.cpp", "bddc_server.cpp", "bddc_setup_gpu.cu", "bddc_coarse.cpp", "bddc_eigen_gpu.cu"]
 
 
 def _nvcc():

@@ -142,6 +142,28 @@ struct LocalMapsBatch {
     std::vector<int> status;  // per subdomain: BDDC_OK or BDDC_E_SETUP
 };
 
+// The adaptive face eigenproblems of a batch on the GPU (bddc_eigen_gpu.cu).
+// Subdomains (those with an adaptive face): the interface Schur complement
+// S^i (n x n row-major) and the weights w; faces: the two subdomains (batch
+// indices), f face dofs with their positions in either subdomain's
+// interface and the net-flux coefficients.  Outputs per face: omega^{ij},
+// the number k of rows above tau and the rows (k x f at o_rows, capacity
+// f x f), before the orthonormalisation against the face's existing rows.
+struct FaceEigenBatch {
+    std::vector<int> n;
+    std::vector<int64_t> o_S, o_w;
+    std::vector<double> S, w;
+    std::vector<int> fi, fj, ff;
+    std::vector<int64_t> o_f, o_rows;  // per face, n_face + 1 entries
+    std::vector<int> pi, pj;
+    std::vector<double> coef;
+    double tau = -1.0;
+    std::vector<double> omega, rows;
+    std::vector<int> nrows, face_status, sub_status;
+};
+using FaceEigenDevice = int (*)(FaceEigenBatch& batch, std::string& err);
+int face_eigen_device(FaceEigenBatch& batch, std::string& err);
+
 // host copy of a device array of doubles (for the host-side export)
 bool device_to_host(const double* dev, int64_t n, double* host);
 using LocalMapsDevice = int (*)(LocalMapsBatch& batch, std::string& err);
@@ -152,7 +174,7 @@ int local_maps_device(LocalMapsBatch& batch, std::string& err);
 // host setup of a batch; with a device hook the dense part of the local
 // maps runs there
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& out,
-                      LocalMapsDevice device = nullptr);
+                      LocalMapsDevice device = nullptr, FaceEigenDevice eig_device = nullptr);
 
 // device part of bddc_setup (bddc_kernels.cu): uploads the host setup of a
 // batch, sizes the persistent launch, and returns the handle

@@ -1523,7 +1523,8 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
         return BDDC_E_CUDA;
     }
     Packed P;
-    SetupResult r = build_all(n_instances, inst, opt, P, local_maps_device);  // dense local maps on the GPU
+    // dense local maps and face eigenproblems on the GPU
+    SetupResult r = build_all(n_instances, inst, opt, P, local_maps_device, face_eigen_device);
     if (r.code) {
         g_setup_err = r.msg;
         return r.code;

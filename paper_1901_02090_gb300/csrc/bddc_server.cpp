@@ -157,14 +157,14 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
     std::vector<bddc_instance> inst;
     for (auto& r : reqs) inst.push_back(r->instance());
     bddc::Packed P;
-    bddc::SetupResult res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device);
+    bddc::SetupResult res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device, bddc::face_eigen_device);
     if (res.code) {
         // find the failing requests: each alone; the others are set up again together
         std::vector<ReqPtr> ok;
         for (auto& r : reqs) {
             bddc::Packed Q;
             const bddc_instance one = r->instance();
-            const bddc::SetupResult rr = bddc::build_all(1, &one, s->opt, Q, bddc::local_maps_device);
+            const bddc::SetupResult rr = bddc::build_all(1, &one, s->opt, Q, bddc::local_maps_device, bddc::face_eigen_device);
             if (rr.code) finish(s, r, rr.code);
             else ok.push_back(r);
         }
@@ -173,7 +173,7 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
         inst.clear();
         for (auto& r : reqs) inst.push_back(r->instance());
         P = bddc::Packed();
-        res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device);
+        res = bddc::build_all((int)inst.size(), inst.data(), s->opt, P, bddc::local_maps_device, bddc::face_eigen_device);
         if (res.code) {
             for (auto& r : reqs) finish(s, r, res.code);
             return;

@@ -1074,7 +1074,7 @@ SetupResult device_local_maps(std::vector<Inst>& I, const std::vector<std::pair<
 }
 
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P,
-                      LocalMapsDevice device) {
+                      LocalMapsDevice device, FaceEigenDevice eig_device) {
     const int nthreads = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     std::vector<Inst> I(n_inst);
     {
@@ -1112,15 +1112,6 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     }
     for (int b = 0; b < n_inst; ++b) weights(I[b], opt.scaling);
     const bool adaptive = opt.tau > 0 && std::isfinite(opt.tau);
-    // Cholesky of every S^i (the face problems need (S^i)^{-1}); always done
-    // so that omega-tilde is reported for the initial constraints too
-    parallel_for((int64_t)tasks.size(), nthreads, [&](int64_t t) {
-        auto [b, s] = tasks[t];
-        Sub& S = I[b].subs[s];
-        S.Lchol = S.S;
-        if (!chol(S.ng, S.Lchol.data())) fail({BDDC_E_SETUP, "interface Schur complement not positive definite"}, b, s);
-    });
-    if (err.code) return err;
     {
         std::vector<std::pair<int, int>> ftasks;
         for (int b = 0; b < n_inst; ++b)
@@ -1128,10 +1119,79 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                 if (!I[b].faces[fi].dir) ftasks.emplace_back(b, fi);
         std::vector<std::vector<std::vector<double>>> rows(ftasks.size());
         std::vector<double> om(ftasks.size(), 0.0);
-        parallel_for((int64_t)ftasks.size(), nthreads, [&](int64_t t) {
-            auto [b, fi] = ftasks[t];
-            om[t] = adaptive_face(I[b], I[b].faces[fi], adaptive ? opt.tau : -1.0, rows[t]);
-        });
+        if (eig_device && !ftasks.empty()) {
+            // the face eigenproblems on the GPU, batched over all faces (the
+            // rows are orthonormalised against the face's rows here)
+            FaceEigenBatch B;
+            std::vector<int64_t> sub0(n_inst + 1, 0);
+            for (int b = 0; b < n_inst; ++b) sub0[b + 1] = sub0[b] + I[b].N;
+            B.n.resize(sub0[n_inst]);
+            B.o_S.assign(1, 0);
+            B.o_w.assign(1, 0);
+            for (int b = 0; b < n_inst; ++b)
+                for (int q = 0; q < I[b].N; ++q) {
+                    const Sub& S = I[b].subs[q];
+                    B.n[sub0[b] + q] = S.ng;
+                    B.o_S.push_back(B.o_S.back() + (int64_t)S.ng * S.ng);
+                    B.o_w.push_back(B.o_w.back() + S.ng);
+                }
+            B.S.resize(B.o_S.back());
+            B.w.resize(B.o_w.back());
+            parallel_for(n_inst, nthreads, [&](int64_t b) {
+                for (int q = 0; q < I[b].N; ++q) {
+                    const Sub& S = I[b].subs[q];
+                    std::copy(S.S.begin(), S.S.end(), B.S.begin() + B.o_S[sub0[b] + q]);
+                    std::copy(S.w.begin(), S.w.end(), B.w.begin() + B.o_w[sub0[b] + q]);
+                }
+            });
+            B.o_f.assign(1, 0);
+            B.o_rows.assign(1, 0);
+            for (auto [b, fi] : ftasks) {
+                const Face& F = I[b].faces[fi];
+                const Sub& Si = I[b].subs[F.i];
+                const Sub& Sj = I[b].subs[F.j];
+                const int f = (int)F.gidx.size();
+                B.fi.push_back((int)(sub0[b] + F.i));
+                B.fj.push_back((int)(sub0[b] + F.j));
+                B.ff.push_back(f);
+                for (int q = 0; q < f; ++q) {
+                    B.pi.push_back((int)(std::lower_bound(Si.gidx.begin(), Si.gidx.end(), F.gidx[q]) - Si.gidx.begin()));
+                    B.pj.push_back((int)(std::lower_bound(Sj.gidx.begin(), Sj.gidx.end(), F.gidx[q]) - Sj.gidx.begin()));
+                    B.coef.push_back(F.coef[q]);
+                }
+                B.o_f.push_back(B.o_f.back() + f);
+                B.o_rows.push_back(B.o_rows.back() + (int64_t)f * f);
+            }
+            B.tau = adaptive ? opt.tau : -1.0;
+            std::string msg;
+            const int rc = eig_device(B, msg);
+            if (rc) return {rc, "face eigenproblems on the device: " + msg};
+            parallel_for((int64_t)ftasks.size(), nthreads, [&](int64_t t) {
+                auto [b, fi] = ftasks[t];
+                const Face& F = I[b].faces[fi];
+                const int f = B.ff[t];
+                std::vector<std::vector<double>> raw(B.nrows[t], std::vector<double>(f));
+                for (int l = 0; l < B.nrows[t]; ++l)
+                    std::copy(B.rows.begin() + B.o_rows[t] + (int64_t)l * f,
+                              B.rows.begin() + B.o_rows[t] + (int64_t)(l + 1) * f, raw[l].begin());
+                om[t] = B.omega[t];
+                rows[t] = orthonormalize(F.rows, raw);
+            });
+        } else {
+            // Cholesky of every S^i (the face problems need (S^i)^{-1}); always
+            // done so that omega-tilde is reported for the initial constraints too
+            parallel_for((int64_t)tasks.size(), nthreads, [&](int64_t t) {
+                auto [b, s] = tasks[t];
+                Sub& S = I[b].subs[s];
+                S.Lchol = S.S;
+                if (!chol(S.ng, S.Lchol.data())) fail({BDDC_E_SETUP, "interface Schur complement not positive definite"}, b, s);
+            });
+            if (err.code) return err;
+            parallel_for((int64_t)ftasks.size(), nthreads, [&](int64_t t) {
+                auto [b, fi] = ftasks[t];
+                om[t] = adaptive_face(I[b], I[b].faces[fi], adaptive ? opt.tau : -1.0, rows[t]);
+            });
+        }
         for (size_t t = 0; t < ftasks.size(); ++t) {
             auto [b, fi] = ftasks[t];
             I[b].omega = std::max(I[b].omega, om[t]);
@@ -1467,7 +1527,7 @@ static int host_setup_create(int n_instances, const bddc_instance* inst, const b
     if (opt_in) opt = *opt_in;
     if (opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE) return BDDC_E_INVALID_ARG;
     auto* hs = new bddc_host_setup();
-    bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P, device);
+    bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P, device, device ? bddc::face_eigen_device : nullptr);
     if (r.code) {
         g_setup_err = r.msg;
         delete hs;

@@ -89,6 +89,36 @@ def test_sparse_and_dense_coarse_solvers_agree_with_oracle(bddc, case, precision
     assert _rel(fs, fd) <= 1e-7 and _rel(ps, pd) <= 1e-7
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sparse_coarse_batch_of_uneven_instances_equals_alone(bddc, precision):
+    """2D and 3D instances of different sizes (different dissection trees and
+    depths) in one launch with the sparse coarse solver: every instance gets
+    bitwise the result of its solo solve."""
+    pbs = [make_config("c1"), _box3d(20, 20, 15), make_config("c2", seed=2095), make_config("tiny3d"),
+           make_config("pin2d")]
+    opt = bddc.default_options(tau=10.0, precision=precision, coarse_solver=bddc.BDDC_COARSE_SPARSE)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def run(group):
+        h = bddc.setup(group, opt, stream=stream)
+        f = np.concatenate([pb.f for pb in group])
+        bc = np.concatenate([pb.bc_value for pb in group])
+        flux, pres = np.empty(len(bc)), np.empty(len(f))
+        its = np.zeros(len(group), dtype=np.int32)
+        assert h.solve(f, bc, 1e-8, flux, pres, its, check=False) == bddc.BDDC_OK
+        h.close()
+        return flux, pres, its
+
+    flux, pres, its = run(pbs)
+    fo = np.cumsum([0] + [len(pb.bc_value) for pb in pbs])
+    co = np.cumsum([0] + [pb.grid.n_cells for pb in pbs])
+    for b, pb in enumerate(pbs):
+        fa, pa, ia = run([pb])
+        assert its[b] == ia[0]
+        assert np.array_equal(flux[fo[b]:fo[b + 1]], fa)
+        assert np.array_equal(pres[co[b]:co[b + 1]], pa)
+
+
 def test_standalone_preconditioner_with_sparse_coarse(bddc):
     pb = make_config("c1")
     o = BDDCOracle(pb, tau=3.0)
