@@ -281,12 +281,14 @@ def serving_run(args, rank):
                         "tau=%g, mixed path; latency includes each request's host setup" % args.tau}
 
 
-def single_path(args, pb1, dev, stream):
-    """The plain FP64 path, one solve per launch: solves/s and p50/p99 latency."""
+def single_path(args, pb1, dev, stream, formulation=0):
+    """The plain FP64 path, one solve per launch: solves/s and p50/p99 latency
+    (formulation 1: the Step-3 operator in its full-space form)."""
     import torch
     from paper_1901_02090_gb300 import bddc
 
-    h1 = bddc.setup([pb1], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64), stream=stream.cuda_stream)
+    h1 = bddc.setup([pb1], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64, formulation=formulation),
+                    stream=stream.cuda_stream)
     f1 = torch.as_tensor(pb1.f, device=dev)
     bc1 = torch.as_tensor(pb1.bc_value, device=dev)
     flux1 = torch.empty(len(pb1.bc_value), dtype=torch.float64, device=dev)
@@ -302,13 +304,13 @@ def single_path(args, pb1, dev, stream):
         torch.cuda.synchronize()
         lat.append(a.elapsed_time(b))
     single_its = h1.stats(0).iterations
-    single_kms = h1.last_solve_timing()[0]
+    single_kms, single_bytes = h1.last_solve_timing()
     h1.close()
     lat_sorted = sorted(lat)
     p50 = lat_sorted[len(lat) // 2]
     p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
     return {"value": 1e3 / statistics.mean(lat), "unit": "solves/s", "p50_ms": p50, "p99_ms": p99,
-            "iterations": single_its, "kernel_ms": single_kms, "solves": len(lat)}
+            "iterations": single_its, "kernel_ms": single_kms, "algorithmic_bytes": single_bytes, "solves": len(lat)}
 
 
 def main():
@@ -388,9 +390,12 @@ def main():
     h.close()
 
     # ---- plain FP64 one-solve-at-a-time path ------------------------------------
-    fp64_single = None
+    fp64_single = full_single = None
     if args.single_solves > 0:
         fp64_single = single_path(args, pbs[0], dev, stream)
+        full_single = single_path(args, pbs[0], dev, stream, bddc.BDDC_FORM_FULL)
+        full_single["note"] = ("the same FP64 solve with the Step-3 operator in its full-space form: the RT0/P0 "
+                               "operator applied matrix-free to the discrete-harmonic extension of each direction")
 
     serving = serving_run(args, rank) if args.serving_requests > 0 else None
 
@@ -413,6 +418,7 @@ def main():
         # ||r|| / ||rhs|| of the full RT0/P0 system at each returned solution (GPU, after the solve)
         "true_relres_max": float(np.max(true_res)),
         "fp64_single": fp64_single,
+        "full_form_single": full_single,
         "serving": serving,
         "latency_batched_ms": {"p50": float(np.percentile(kms, 50)), "p99": float(np.percentile(kms, 99)),
                                "per_step_wall": total_ms / K, "note": "kernel time of one batch (CUDA events)"},

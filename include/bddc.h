@@ -78,6 +78,23 @@ extern "C" {
 #define BDDC_COARSE_SPARSE 2
 #define BDDC_COARSE_DENSE_MAX 2048
 
+/* Form of the Step-3 operator (CG of Algorithm 1 on the divergence-free flux
+ * correction; both forms give the same iterates in exact arithmetic).
+ * Condensed: the interface problem of Sec. 3 (interiors eliminated by
+ * static condensation); each subdomain applies its flux Schur complement
+ * S^i as a dense n_Gamma^2 block.  Full: the iterates live in the full
+ * RT0/P0 space as discrete-harmonic extensions of their interface values.
+ * Each iteration extends the direction into the subdomain interiors
+ * (interior fluxes and cell pressures, the interface columns of the
+ * post-correction map, plus the subdomain's pressure constant) and applies
+ * the mixed operator of Sec. 2 to it matrix-free, face by face; its rows on
+ * the interior faces and cells vanish by construction, and its interface
+ * rows are S^i applied to the direction.  The full form reads
+ * n_Gamma x (n_I + n_cells) extension entries per subdomain instead of
+ * n_Gamma^2 and requires BDDC_PREC_FP64. */
+#define BDDC_FORM_CONDENSED 0
+#define BDDC_FORM_FULL 1
+
 typedef struct {
     int dim;      /* 2 or 3 */
     int n[3];     /* cells per axis; n[2] == 1 in 2D */
@@ -106,6 +123,7 @@ typedef struct {
     int pressure_scaling; /* 1: rescale the pressure block by D (Sec. 4) */
     int n_threads;        /* host threads used by setup; 0 = all cores */
     int coarse_solver;    /* BDDC_COARSE_* */
+    int formulation;      /* BDDC_FORM_*; BDDC_FORM_FULL needs BDDC_PREC_FP64 */
 } bddc_options;
 
 typedef struct {
@@ -128,7 +146,7 @@ typedef struct bddc_handle bddc_handle;
 
 /* Default options: tau = 0 (face averages), multiplicity scaling, FP64,
  * maxit = 5000, pressure scaling on, all host threads, automatic coarse
- * solver. */
+ * solver, condensed operator. */
 void bddc_default_options(bddc_options* opt);
 
 /* Set up one or more independent instances (Algorithm 1 setup: local
@@ -265,8 +283,9 @@ int bddc_host_setup_coarse_solve(const bddc_host_setup* hs, int instance, const 
 /* Diagnostic copy of a device work vector of the last solve into host
  * memory: "x" "r0" "r1" "d0" "d1" "g" "u0" (interface), "ql" "zl" "yl" "rl"
  * "tl" (local slots), "rcl" (coarse slots), "wc" (coarse vectors), "xp" "zp"
- * "prhs" "part_rr" "part_rz" "part_dq" (per subdomain).  *count receives
- * the length; dst may be NULL to query it. */
+ * "prhs" "part_rr" "part_rz" "part_dq" (per subdomain), "alpha" "beta" (the
+ * CG coefficients, maxit + 1 per instance, instance-major).  *count
+ * receives the length; dst may be NULL to query it. */
 int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64_t* count);
 
 /* Diagnostic phase timeline of the last solve: pairs (phase id, global

@@ -36,6 +36,8 @@ BDDC_COARSE_AUTO = 0
 BDDC_COARSE_DENSE = 1
 BDDC_COARSE_SPARSE = 2
 BDDC_COARSE_DENSE_MAX = 2048
+BDDC_FORM_CONDENSED = 0
+BDDC_FORM_FULL = 1
 
 
 class bddc_grid(C.Structure):
@@ -50,7 +52,7 @@ class bddc_instance(C.Structure):
 class bddc_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("scaling", C.c_int), ("precision", C.c_int),
                 ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int),
-                ("coarse_solver", C.c_int)]
+                ("coarse_solver", C.c_int), ("formulation", C.c_int)]
 
 
 class bddc_stats(C.Structure):

@@ -78,6 +78,14 @@ struct Packed {
     std::vector<int> inst_grid;
     std::vector<double> inst_h, cell_kinv;
     std::vector<int8_t> face_bct;
+    // the full-space form of the Step-3 operator (BDDC_FORM_FULL), per local
+    // interface slot: the RT0 mass coefficient h_a^2 / (|K| k_a) of the
+    // slot's face in the subdomain's cell K on it; K's other face along the
+    // same axis as an index into the subdomain's local fluxes (slots, then
+    // ng + interior face) or -1 (a no-flow face); K as local cell r + 1 when
+    // the face is K's lower face, -(r + 1) when it is its upper face
+    std::vector<double> slot_fk;
+    std::vector<int> slot_fopp, slot_fcell;
     // matrices
     std::vector<double> S, F64, P64, Gpre, Gpost, Kinv;
     std::vector<float> F32, P32;
@@ -89,6 +97,15 @@ struct Packed {
     int64_t n_sub = 0, n_gamma = 0, n_coarse_vec = 0;
     int max_ng = 0, max_m = 0, max_ncn = 0, max_out_post = 0, max_in_post = 0;
 };
+
+// the option values every entry point accepts
+inline bool options_valid(const bddc_options& o) {
+    return o.maxit > 0 && (o.precision == BDDC_PREC_FP64 || o.precision == BDDC_PREC_FP32) &&
+           (o.scaling == BDDC_SCALING_MULTIPLICITY || o.scaling == BDDC_SCALING_STIFFNESS) &&
+           o.coarse_solver >= BDDC_COARSE_AUTO && o.coarse_solver <= BDDC_COARSE_SPARSE &&
+           (o.formulation == BDDC_FORM_CONDENSED ||
+            (o.formulation == BDDC_FORM_FULL && o.precision == BDDC_PREC_FP64));
+}
 
 struct SetupResult {
     int code = BDDC_OK;

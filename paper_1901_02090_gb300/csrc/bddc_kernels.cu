@@ -284,11 +284,17 @@ struct PrecFP64 {
     using S_t = double;
     using F_t = double;
     static constexpr bool kMixed = false;
+    static constexpr bool kFull = false;
+};
+// FP64 with the operator in its full-space form (BDDC_FORM_FULL)
+struct PrecFP64Full : PrecFP64 {
+    static constexpr bool kFull = true;
 };
 struct PrecMixed {
     using S_t = float2;   // the operator as an FP32 pair (48 significant bits)
     using F_t = float;
     static constexpr bool kMixed = true;
+    static constexpr bool kFull = false;
 };
 
 // Per-warp shared-memory slice: the staged input vector in FP64 and as an
@@ -301,6 +307,7 @@ struct WarpSm {
     double* xin;
     double* wcs;
     double* tsum;  // per net-flux row sums (mixed path)
+    double* ext;   // full form: the direction's extension (interior fluxes, cell pressures)
 };
 struct CtaSm {
     double* rhs;  // staged coarse right-hand side (CTA-level)
@@ -310,7 +317,7 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     CtaSm c;
     c.rhs = base;
     const int warp = threadIdx.x >> 5;
-    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1);  // in doubles
+    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1) + p.max_ext;  // in doubles
     double* wb = base + p.max_ncn + (int64_t)warp * per_warp;
     c.w.x = wb;
     c.w.xh = reinterpret_cast<float*>(wb + p.max_ng);
@@ -318,6 +325,7 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     c.w.xin = wb + 2 * p.max_ng;
     c.w.wcs = c.w.xin + p.max_in_post;
     c.w.tsum = c.w.wcs + p.max_m + 1;
+    c.w.ext = c.w.tsum + p.max_m + 1;
     return c;
 }
 
@@ -734,6 +742,72 @@ __device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     return true;
 }
 
+// Full-space form of the same phase (BDDC_FORM_FULL, FP64).  The direction
+// d on the interface and its pressure constant p_0 define a vector of the
+// full RT0/P0 space: interior fluxes and cell pressures from the discrete
+// harmonic extension (the interface columns of the post-correction map
+// G_post; cell pressure d_s (p_0 + extension)).  The mixed operator of
+// Sec. 2 applied to it has nonzero rows only on the interface faces; each
+// such face of the subdomain has one cell K here, and its row is the face's
+// row of K's RT0 mass block, h_a^2 / (|K| k_a) (u_e / 3 + u_opp / 6), plus
+// +p_K if the face is K's lower face, -p_K if its upper face.  Equal to
+// S^i d + d_s sigma p_0 up to rounding (the condensed form).
+template <class PR>
+__device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
+    const int b = p.sub_inst[s];
+    if (inst_done(p, b)) return false;
+    const int l = threadIdx.x & 31;
+    const double beta = __ldcg(p.beta_hist + (int64_t)b * (p.maxit + 1) + k);
+    double* dold = (k & 1) ? p.dbuf0 : p.dbuf1;
+    double* dnew = (k & 1) ? p.dbuf1 : p.dbuf0;
+    double* dpold = (k & 1) ? p.dp0 : p.dp1;
+    double* dpnew = (k & 1) ? p.dp1 : p.dp0;
+    const int ng = p.sub_ng[s], ni = p.sub_ni[s], nc = p.sub_nc[s];
+    const int64_t so = p.off_slot[s];
+    for (int kk = l; kk < ng; kk += 32) {
+        const int pt = p.slot_partner[so + kk];
+        const int gi = p.slot_g[so + kk];
+        const double z = __ldcg(p.zl + so + kk) + (pt >= 0 ? __ldcg(p.zl + pt) : 0.0);
+        const double dn = (k == 0) ? z : z + beta * __ldcg(dold + gi);
+        if (slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
+        w.x[kk] = dn;
+    }
+    const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
+    if (l == 0) dpnew[s] = dpn;
+    __syncwarp();
+    // extension: column j of G_post (input-major) holds the outputs of
+    // interface input j, interior fluxes then cell pressures
+    const double* G = p.Gpost + p.off_Gpost[s];
+    const int no = ni + nc;
+    for (int o = l; o < no; o += 32) {
+        double a0 = 0.0, a1 = 0.0;
+        int j = 0;
+        for (; j + 1 < ng; j += 2) {
+            a0 = fma(__ldg(G + (int64_t)j * no + o), w.x[j], a0);
+            a1 = fma(__ldg(G + (int64_t)(j + 1) * no + o), w.x[j + 1], a1);
+        }
+        if (j < ng) a0 = fma(__ldg(G + (int64_t)j * no + o), w.x[j], a0);
+        w.ext[o] = a0 + a1;
+    }
+    __syncwarp();
+    constexpr double kThird = 1.0 / 3.0, kSixth = 1.0 / 6.0;
+    const double ds = p.sub_d[s];
+    double dq = 0.0;
+    for (int kk = l; kk < ng; kk += 32) {
+        const int op = p.slot_fopp[so + kk], pc = p.slot_fcell[so + kk];
+        const double ue = w.x[kk];
+        const double uo = op < 0 ? 0.0 : (op < ng ? w.x[op] : w.ext[op - ng]);
+        const double pk = ds * (dpn + w.ext[ni + (pc > 0 ? pc : -pc) - 1]);
+        const double q = p.slot_fk[so + kk] * (kThird * ue + kSixth * uo) + (pc > 0 ? pk : -pk);
+        p.ql[so + kk] = q;
+        dq += ue * q;
+    }
+    dq = warp_sum(dq);
+    if (l == 0) p.part_dq[s] = dq;
+    __syncwarp();
+    return true;
+}
+
 template <class PR>
 __device__ bool ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
     const int b = p.sub_inst[s];
@@ -1091,6 +1165,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         if (__ldcg(p.n_active) <= 0) break;
         cg_phase(kCtrDQ, k, [&](int64_t s) -> bool {
             if constexpr (MX) return mx_dirop(p, s, k, w);
+            else if constexpr (PR::kFull) return ph_dirop_full<PR>(p, s, k, w);
             else return ph_dirop<PR>(p, s, k, w);
         });
         if (!phase_end(p, 8, nts)) return;
@@ -1394,7 +1469,7 @@ using namespace bddc;
 struct bddc_handle {
     cudaStream_t stream = nullptr;
     int device = 0;
-    int n_inst = 0, maxit = 0, precision = 0;
+    int n_inst = 0, maxit = 0, precision = 0, formulation = BDDC_FORM_CONDENSED;
     Packed P;
     Params prm{};
     std::vector<void*> allocs;
@@ -1483,6 +1558,7 @@ void bddc_default_options(bddc_options* opt) {
     opt->pressure_scaling = 1;
     opt->n_threads = 0;
     opt->coarse_solver = BDDC_COARSE_AUTO;
+    opt->formulation = BDDC_FORM_CONDENSED;
 }
 
 const char* bddc_error_string(int code) {
@@ -1513,10 +1589,7 @@ int bddc_setup(int n_instances, const bddc_instance* inst, const bddc_options* o
     bddc_options opt;
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.maxit <= 0 || (opt.precision != BDDC_PREC_FP64 && opt.precision != BDDC_PREC_FP32) ||
-        (opt.scaling != BDDC_SCALING_MULTIPLICITY && opt.scaling != BDDC_SCALING_STIFFNESS) ||
-        opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE)
-        return BDDC_E_INVALID_ARG;
+    if (!bddc::options_valid(opt)) return BDDC_E_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -1548,6 +1621,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     h->n_inst = n_instances;
     h->maxit = opt.maxit;
     h->precision = opt.precision;
+    h->formulation = opt.formulation;
     h->P = std::move(packed);
     Packed& P = h->P;
     for (int b = 0; b < n_instances; ++b) {
@@ -1578,6 +1652,9 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     UP(slot_dsig, P.slot_dsig); UP(cslot_c, P.cslot_c); UP(cell_gid, P.cell_gid); UP(int_fid, P.int_fid);
     UP(g_fid, P.g_fid); UP(g_bsign, P.g_bsign); UP(c_slot_a, P.c_slot_a); UP(c_slot_b, P.c_slot_b);
     UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0);
+    if (opt.formulation == BDDC_FORM_FULL) {
+        UP(slot_fk, P.slot_fk); UP(slot_fopp, P.slot_fopp); UP(slot_fcell, P.slot_fcell);
+    }
     UP(Gpre, P.Gpre); UP(P64, P.P64);
     if (P.dev_Gpost) {  // computed on the device by the setup: adopted, freed with the handle's Packed
         p.Gpost = P.dev_Gpost.get();
@@ -1736,14 +1813,16 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     p.max_in_post = std::max(P.max_in_post, 1);
     p.max_ncn = P.coarse_sparse ? 2 : std::max(P.max_ncn, 1);  // the CTA rhs area of the dense coarse solve
     p.max_m = std::max(P.max_m, 1);
-    h->smem = sizeof(double) * ((size_t)p.max_ncn +
-                                (size_t)kWarps * (2 * (size_t)p.max_ng + p.max_in_post + 2 * ((size_t)p.max_m + 1)));
+    p.max_ext = opt.formulation == BDDC_FORM_FULL ? std::max(P.max_out_post, 1) : 0;
+    h->smem = sizeof(double) * ((size_t)p.max_ncn + (size_t)kWarps * (2 * (size_t)p.max_ng + p.max_in_post +
+                                                                       2 * ((size_t)p.max_m + 1) + p.max_ext));
     if (h->smem > 200 * 1024) {
         bddc_destroy(h);
         return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve
     }
-    const void* kfn = opt.precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<PrecMixed>
-                                                      : (const void*)bddc_solve_kernel<PrecFP64>;
+    const void* kfn = opt.precision == BDDC_PREC_FP32     ? (const void*)bddc_solve_kernel<PrecMixed>
+                      : opt.formulation == BDDC_FORM_FULL ? (const void*)bddc_solve_kernel<PrecFP64Full>
+                                                          : (const void*)bddc_solve_kernel<PrecFP64>;
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     int nb = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, h->smem);
@@ -1803,7 +1882,10 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     double it_b = 0.0, pre_b = 0.0, post_b = 0.0;
     for (int64_t s = 0; s < NS; ++s) {
         const double ng = P.sub_ng[s], m = P.sub_m[s], nc = P.sub_nc[s], ni = P.sub_ni[s];
-        it_b += 8.0 * ng * ng + fb * ng * ng + 2.0 * fb * m * ng + 8.0 * 18.0 * ng;
+        // the operator: S^i, or in the full form the extension's n_Gamma
+        // columns of G_post and the per-slot face data (16 bytes)
+        const double op_b = opt.formulation == BDDC_FORM_FULL ? 8.0 * ng * (ni + nc) + 16.0 * ng : 8.0 * ng * ng;
+        it_b += op_b + fb * ng * ng + 2.0 * fb * m * ng + 8.0 * 18.0 * ng;
         // the source columns of G_pre and G_post are not counted: they are
         // skipped for source-free subdomains
         pre_b += 3.0 * fb * m * ng + 8.0 * ng * ng + fb * ng * ng + 8.0 * 20.0 * ng;
@@ -1882,8 +1964,9 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     cudaMemsetAsync(p.tstamp, 0, 2 * sizeof(long long) * (size_t)p.tstamp_cap, st);
     cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);
     void* args[] = {&p};
-    const void* kfn = h->precision == BDDC_PREC_FP32 ? (const void*)bddc_solve_kernel<PrecMixed>
-                                                     : (const void*)bddc_solve_kernel<PrecFP64>;
+    const void* kfn = h->precision == BDDC_PREC_FP32       ? (const void*)bddc_solve_kernel<PrecMixed>
+                      : h->formulation == BDDC_FORM_FULL ? (const void*)bddc_solve_kernel<PrecFP64Full>
+                                                         : (const void*)bddc_solve_kernel<PrecFP64>;
     cudaEventRecord(h->ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(h->grid), dim3(kThreads), args, h->smem, st);
     cudaEventRecord(h->ev1, st);
@@ -2000,6 +2083,8 @@ int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64
     else if (n == "part_rr") { src = p.part_rr; len = NS; }
     else if (n == "part_rz") { src = p.part_rz; len = NS; }
     else if (n == "part_dq") { src = p.part_dq; len = NS; }
+    else if (n == "alpha") { src = p.alpha_hist; len = (int64_t)h->n_inst * (p.maxit + 1); }
+    else if (n == "beta") { src = p.beta_hist; len = (int64_t)h->n_inst * (p.maxit + 1); }
     else return BDDC_E_INVALID_ARG;
     if (count) *count = len;
     if (dst && len) {

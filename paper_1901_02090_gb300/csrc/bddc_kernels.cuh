@@ -73,6 +73,11 @@ struct Params {
     const int64_t *cell_gid, *int_fid, *g_fid;
     const double* g_bsign;
     const int *c_slot_a, *c_slot_b;
+    // full-space form of the operator (BDDC_FORM_FULL): per slot the RT0 mass
+    // coefficient of its face in its cell, the cell's other face along the
+    // axis and the cell with the face's side (see the setup's Packed)
+    const double* slot_fk;
+    const int *slot_fopp, *slot_fcell;
     // coarse units
     int64_t n_cunits;
     const int *cunit_inst, *cunit_row0;
@@ -133,6 +138,7 @@ struct Params {
     int maxit;
     double tol;
     int max_ng, max_in_post, max_ncn, max_m;
+    int max_ext;  // per-warp extension area (full form: max n_I + n_cells; else 0)
 };
 
 }  // namespace bddc

@@ -337,10 +337,7 @@ int bddc_server_create(const bddc_options* opt_in, size_t hbm_budget_bytes, int 
     bddc_options opt;
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.maxit <= 0 || (opt.precision != BDDC_PREC_FP64 && opt.precision != BDDC_PREC_FP32) ||
-        (opt.scaling != BDDC_SCALING_MULTIPLICITY && opt.scaling != BDDC_SCALING_STIFFNESS) ||
-        opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE)
-        return BDDC_E_INVALID_ARG;
+    if (!bddc::options_valid(opt)) return BDDC_E_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();

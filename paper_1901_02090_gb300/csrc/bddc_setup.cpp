@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <unordered_map>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -1316,6 +1317,29 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                 if (sa[g] < 0) sa[g] = (int)(slot + k); else sb[g] = (int)(slot + k);
             }
             {
+                // full-space form: the cell of S on each interface face and
+                // that cell's other face along the face's axis
+                std::unordered_map<int64_t, int> floc, cloc;
+                for (int q = 0; q < S.ng + S.ni; ++q) floc[S.faces[q]] = q;
+                for (int r = 0; r < S.nc; ++r) cloc[S.cells[r]] = r;
+                for (int k = 0; k < S.ng; ++k) {
+                    const int64_t f = S.faces[k];
+                    int ax = 0;
+                    int64_t K = In.geo.face_cell(f, 1, &ax);  // the cell above f
+                    const bool lower = K >= 0 && cloc.count(K) > 0;
+                    if (!lower) K = In.geo.face_cell(f, 0, &ax);
+                    if (K < 0 || cloc.count(K) == 0) return {BDDC_E_SETUP, "interface face without a cell of its subdomain"};
+                    const int64_t opp = In.geo.cell_face(K, ax, lower ? 1 : 0);
+                    const auto it = floc.find(opp);
+                    if (it == floc.end() && In.bct[opp] != 0)
+                        return {BDDC_E_SETUP, "a cell face that is neither a subdomain unknown nor a no-flow face"};
+                    const int r = cloc[K];
+                    P.slot_fopp.push_back(it == floc.end() ? -1 : it->second);
+                    P.slot_fcell.push_back(lower ? r + 1 : -(r + 1));
+                    P.slot_fk.push_back(In.geo.h[ax] * In.geo.h[ax] / In.geo.vol * In.kinv[(size_t)K * In.geo.dim + ax]);
+                }
+            }
+            {
                 int start = 0;
                 for (int a = 0; a < S.m; ++a) {
                     if (S.rown[a] == 0) { P.cslot_fstart.push_back(-1); continue; }
@@ -1443,6 +1467,7 @@ bool export_named(const bddc::Packed& P, const char* name, void* dst, int64_t* c
     E(inst_face_off); E(inst_nfaces); E(inst_cell_off); E(inst_ncells); E(off_S); E(off_F); E(off_P);
     E(off_Gpre); E(off_Gpost); E(off_slot); E(off_cslot); E(off_cell); E(off_int); E(cell_gid); E(int_fid); E(g_fid);
     E(inst_vol); E(inst_omega); E(sub_d); E(slot_w); E(slot_dsig); E(g_bsign); E(S); E(Gpre); E(Gpost); E(Kinv); E(P64);
+    E(slot_fk); E(slot_fopp); E(slot_fcell);
     E(inst_csoff); E(inst_node0); E(cn_inst); E(cn_p); E(cn_q); E(cn_depth); E(cn_off_dof); E(cn_off_X); E(cn_off_H);
     E(cn_off_u); E(cn_dof); E(cn_c0); E(cn_c1); E(cn_X); E(cn_H); E(cn_HT);
 #undef E
@@ -1525,7 +1550,7 @@ static int host_setup_create(int n_instances, const bddc_instance* inst, const b
     bddc_options opt;
     bddc_default_options(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.coarse_solver < BDDC_COARSE_AUTO || opt.coarse_solver > BDDC_COARSE_SPARSE) return BDDC_E_INVALID_ARG;
+    if (!bddc::options_valid(opt)) return BDDC_E_INVALID_ARG;
     auto* hs = new bddc_host_setup();
     bddc::SetupResult r = bddc::build_all(n_instances, inst, opt, hs->P, device, device ? bddc::face_eigen_device : nullptr);
     if (r.code) {

@@ -21,7 +21,8 @@ class Packed:
                      "inst_cell_off", "inst_ncells", "off_S", "off_F", "off_P", "off_Gpre", "off_Gpost",
                      "off_slot", "off_cslot", "off_cell", "off_int", "cell_gid", "int_fid", "g_fid",
                      "inst_vol", "sub_d", "slot_w", "slot_dsig", "g_bsign", "S", "F", "P", "Gpre",
-                     "Gpost", "Kinv", "slot_fcs", "cslot_n", "slot_coef", "P64"):
+                     "Gpost", "Kinv", "slot_fcs", "cslot_n", "slot_coef", "P64",
+                     "slot_fk", "slot_fopp", "slot_fcell"):
             setattr(self, name, hs.get(name))
         # sparse coarse solver: no dense inverse; coarse solves go through
         # the host sweeps over the packed multifrontal factor
@@ -41,8 +42,28 @@ class Packed:
         return np.arange(a, b)
 
 
-def emulate_solve(P: Packed, f, bc, tol, maxit=5000, mixed=False):
+def full_form_apply(P: Packed, s, d, dp):
+    """Interface rows of the full-space form of the Step-3 operator for
+    subdomain s (BDDC_FORM_FULL): the direction d (local slots) and its
+    pressure constant dp extended into the subdomain by the interface columns
+    of G_post, then per interface face the row of its cell's RT0 mass block
+    plus the cell's +-pressure, from the exported per-slot face data."""
+    ng, ni, nc = int(P.sub_ng[s]), int(P.sub_ni[s]), int(P.sub_nc[s])
+    sl = P.slots(s)
+    G = P.mat(P.Gpost, P.off_Gpost, s, ng + nc, ni + nc)
+    ext = G[:, :ng] @ d
+    loc = np.concatenate([d, ext[:ni]])
+    fk, fo, fc = P.slot_fk[sl], P.slot_fopp[sl], P.slot_fcell[sl]
+    uo = np.where(fo >= 0, loc[np.maximum(fo, 0)], 0.0)
+    pk = P.sub_d[s] * (dp + ext[ni + np.abs(fc) - 1])
+    return fk * (d / 3.0 + uo / 6.0) + np.sign(fc) * pk
+
+
+def emulate_solve(P: Packed, f, bc, tol, maxit=5000, mixed=False, full_form=False):
     """Returns (flux, pressure, iterations per instance, alphas, betas).
+
+    full_form=True applies the Step-3 operator in its full-space form
+    (full_form_apply) instead of S^i.
 
     mixed=True replays the mixed-precision kernel: F and Psi applied as
     P_Z F P_Z and Psi_0 + P_Z Psi (P_Z removes each face's net flux, Psi_0
@@ -152,6 +173,8 @@ def emulate_solve(P: Packed, f, bc, tol, maxit=5000, mixed=False):
         return z, zp
 
     def op(d, dp):
+        if full_form:
+            return assemble([full_form_apply(P, s, d[gl[s]], dp[s]) for s in range(ns)])
         return assemble([S[s] @ d[gl[s]] + P.slot_dsig[slots[s]] * dp[s] for s in range(ns)])
 
     # PCG per instance (instances are independent; run them jointly)
