@@ -306,18 +306,19 @@ struct WarpSm {
     float* xl;
     double* xin;
     double* wcs;
-    double* tsum;  // per net-flux row sums (mixed path)
-    double* ext;   // full form: the direction's extension (interior fluxes, cell pressures)
+    double* tsum;  // per net-flux row sums (mixed path); the full form's extension follows
 };
 struct CtaSm {
     double* rhs;  // staged coarse right-hand side (CTA-level)
     WarpSm w;
 };
+// kExt: the warp areas include the full form's extension (max_ext doubles)
+template <bool kExt = false>
 __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     CtaSm c;
     c.rhs = base;
     const int warp = threadIdx.x >> 5;
-    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1) + p.max_ext;  // in doubles
+    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1) + (kExt ? p.max_ext : 0);  // in doubles
     double* wb = base + p.max_ncn + (int64_t)warp * per_warp;
     c.w.x = wb;
     c.w.xh = reinterpret_cast<float*>(wb + p.max_ng);
@@ -325,7 +326,6 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     c.w.xin = wb + 2 * p.max_ng;
     c.w.wcs = c.w.xin + p.max_in_post;
     c.w.tsum = c.w.wcs + p.max_m + 1;
-    c.w.ext = c.w.tsum + p.max_m + 1;
     return c;
 }
 
@@ -776,7 +776,9 @@ __device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
     if (l == 0) dpnew[s] = dpn;
     __syncwarp();
     // extension: column j of G_post (input-major) holds the outputs of
-    // interface input j, interior fluxes then cell pressures
+    // interface input j, interior fluxes then cell pressures; staged in the
+    // warp's area after tsum (max_ext doubles)
+    double* ext = w.tsum + p.max_m + 1;
     const double* G = p.Gpost + p.off_Gpost[s];
     const int no = ni + nc;
     for (int o = l; o < no; o += 32) {
@@ -787,7 +789,7 @@ __device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
             a1 = fma(__ldg(G + (int64_t)(j + 1) * no + o), w.x[j + 1], a1);
         }
         if (j < ng) a0 = fma(__ldg(G + (int64_t)j * no + o), w.x[j], a0);
-        w.ext[o] = a0 + a1;
+        ext[o] = a0 + a1;
     }
     __syncwarp();
     constexpr double kThird = 1.0 / 3.0, kSixth = 1.0 / 6.0;
@@ -796,8 +798,8 @@ __device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
     for (int kk = l; kk < ng; kk += 32) {
         const int op = p.slot_fopp[so + kk], pc = p.slot_fcell[so + kk];
         const double ue = w.x[kk];
-        const double uo = op < 0 ? 0.0 : (op < ng ? w.x[op] : w.ext[op - ng]);
-        const double pk = ds * (dpn + w.ext[ni + (pc > 0 ? pc : -pc) - 1]);
+        const double uo = op < 0 ? 0.0 : (op < ng ? w.x[op] : ext[op - ng]);
+        const double pk = ds * (dpn + ext[ni + (pc > 0 ? pc : -pc) - 1]);
         const double q = p.slot_fk[so + kk] * (kThird * ue + kSixth * uo) + (pc > 0 ? pk : -pk);
         p.ql[so + kk] = q;
         dq += ue * q;
@@ -1066,7 +1068,7 @@ template <class PR>
 __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     constexpr bool MX = PR::kMixed;
     extern __shared__ double smem_base[];
-    CtaSm sm = carve(p, smem_base);
+    CtaSm sm = carve<PR::kFull>(p, smem_base);
     WarpSm& w = sm.w;
     int64_t a, e;
     int staged;
