@@ -78,7 +78,7 @@ struct Packed {
     std::vector<int> inst_grid;
     std::vector<double> inst_h, cell_kinv;
     std::vector<int8_t> face_bct;
-    // the full-space form of the Step-3 operator (BDDC_FORM_FULL), per local
+    // the full-space form of the Step-3 operator (BDDC_FORM_FULL only), per local
     // interface slot: the RT0 mass coefficient h_a^2 / (|K| k_a) of the
     // slot's face in the subdomain's cell K on it; K's other face along the
     // same axis as an index into the subdomain's local fluxes (slots, then

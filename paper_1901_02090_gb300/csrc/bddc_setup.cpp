@@ -34,7 +34,6 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
-#include <unordered_map>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -1316,25 +1315,39 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                 P.slot_coef.push_back(S.fcoef[k]);
                 if (sa[g] < 0) sa[g] = (int)(slot + k); else sb[g] = (int)(slot + k);
             }
-            {
+            if (opt.formulation == BDDC_FORM_FULL) {
                 // full-space form: the cell of S on each interface face and
-                // that cell's other face along the face's axis
-                std::unordered_map<int64_t, int> floc, cloc;
-                for (int q = 0; q < S.ng + S.ni; ++q) floc[S.faces[q]] = q;
-                for (int r = 0; r < S.nc; ++r) cloc[S.cells[r]] = r;
+                // that cell's other face along the face's axis (S.faces holds
+                // the interface faces sorted, then the interior ones sorted;
+                // S.cells is sorted)
+                auto face_pos = [&](int64_t f) -> int {
+                    auto it = std::lower_bound(S.faces.begin(), S.faces.begin() + S.ng, f);
+                    if (it != S.faces.begin() + S.ng && *it == f) return (int)(it - S.faces.begin());
+                    it = std::lower_bound(S.faces.begin() + S.ng, S.faces.end(), f);
+                    if (it != S.faces.end() && *it == f) return (int)(it - S.faces.begin());
+                    return -1;
+                };
+                auto cell_pos = [&](int64_t c) -> int {
+                    if (c < 0) return -1;
+                    const auto it = std::lower_bound(S.cells.begin(), S.cells.end(), c);
+                    return (it != S.cells.end() && *it == c) ? (int)(it - S.cells.begin()) : -1;
+                };
                 for (int k = 0; k < S.ng; ++k) {
                     const int64_t f = S.faces[k];
                     int ax = 0;
                     int64_t K = In.geo.face_cell(f, 1, &ax);  // the cell above f
-                    const bool lower = K >= 0 && cloc.count(K) > 0;
-                    if (!lower) K = In.geo.face_cell(f, 0, &ax);
-                    if (K < 0 || cloc.count(K) == 0) return {BDDC_E_SETUP, "interface face without a cell of its subdomain"};
+                    int r = cell_pos(K);
+                    const bool lower = r >= 0;
+                    if (!lower) {
+                        K = In.geo.face_cell(f, 0, &ax);
+                        r = cell_pos(K);
+                    }
+                    if (r < 0) return {BDDC_E_SETUP, "interface face without a cell of its subdomain"};
                     const int64_t opp = In.geo.cell_face(K, ax, lower ? 1 : 0);
-                    const auto it = floc.find(opp);
-                    if (it == floc.end() && In.bct[opp] != 0)
+                    const int o = face_pos(opp);
+                    if (o < 0 && In.bct[opp] != 0)
                         return {BDDC_E_SETUP, "a cell face that is neither a subdomain unknown nor a no-flow face"};
-                    const int r = cloc[K];
-                    P.slot_fopp.push_back(it == floc.end() ? -1 : it->second);
+                    P.slot_fopp.push_back(o);
                     P.slot_fcell.push_back(lower ? r + 1 : -(r + 1));
                     P.slot_fk.push_back(In.geo.h[ax] * In.geo.h[ax] / In.geo.vol * In.kinv[(size_t)K * In.geo.dim + ax]);
                 }

@@ -22,6 +22,7 @@ from test_native_setup import CASES
 
 
 def _setup(pb, **kw):
+    kw.setdefault("formulation", bddc.BDDC_FORM_FULL)
     return Packed(bddc.HostSetup([pb], bddc.default_options(tau=4.0, **kw)))
 
 
@@ -81,6 +82,7 @@ def test_full_form_pcg_reaches_the_oracle_solution(case):
     assert np.linalg.norm(flux - r.flux) <= 1e-9 * np.linalg.norm(r.flux)
     assert np.linalg.norm(pres - r.pressure) <= 1e-8 * np.linalg.norm(r.pressure)
     # the same iterates as the condensed form: the first CG coefficients agree
+    # (the setup of the full form carries everything the condensed form uses)
     _, _, its1, al1, _ = emulate_solve(P, pb.f, pb.bc_value, 1e-12)
     n = min(6, len(al[0]), len(al1[0]))
     assert np.allclose(al[0][:n], al1[0][:n], rtol=1e-9, atol=0)
@@ -94,3 +96,8 @@ def test_full_form_needs_fp64():
     with pytest.raises(bddc.BDDCError) as e:
         bddc.HostSetup([pb], bddc.default_options(formulation=7))
     assert e.value.code == bddc.BDDC_E_INVALID_ARG
+
+
+def test_condensed_setup_builds_no_face_data():
+    P = Packed(bddc.HostSetup([CASES["c1"]()], bddc.default_options(tau=4.0)))
+    assert len(P.slot_fk) == 0 and len(P.slot_fopp) == 0 and len(P.slot_fcell) == 0
