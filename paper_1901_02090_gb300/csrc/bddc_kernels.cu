@@ -33,6 +33,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bddc_internal.hpp"
@@ -1733,13 +1734,23 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
 #undef UP
     if (!rc) {
         if (opt.precision == BDDC_PREC_FP32) {
-            // S and the coarse inverse as FP32 pairs (hi, lo); F and Psi FP32
-            auto pairs = [](const std::vector<double>& v) {
+            // S and the coarse inverse as FP32 pairs (hi, lo); F and Psi FP32.
+            // The conversion runs on the setup's host threads (GBs for large
+            // batches).
+            const int nth = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+            auto pairs = [nth](const std::vector<double>& v) {
                 std::vector<float2> o(v.size());
-                for (size_t q = 0; q < v.size(); ++q) {
-                    const float hi = (float)v[q];
-                    o[q] = make_float2(hi, (float)(v[q] - (double)hi));
-                }
+                const size_t n = v.size();
+                const size_t T = (size_t)std::max<int64_t>(1, std::min<int64_t>(nth, (int64_t)(n >> 16) + 1));
+                std::vector<std::thread> th;
+                for (size_t t = 0; t < T; ++t)
+                    th.emplace_back([&v, &o, n, T, t] {
+                        for (size_t q = n * t / T; q < n * (t + 1) / T; ++q) {
+                            const float hi = (float)v[q];
+                            o[q] = make_float2(hi, (float)(v[q] - (double)hi));
+                        }
+                    });
+                for (std::thread& x : th) x.join();
                 return o;
             };
             const float *f = nullptr, *pp = nullptr;

@@ -1252,7 +1252,6 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             for (int a = 0; a < 3; ++a) P.cell_kinv.push_back(a < In.geo.dim ? In.kinv[(size_t)c * In.geo.dim + a] : 0.0);
         P.face_bct.insert(P.face_bct.end(), In.bct.begin(), In.bct.end());
         P.max_ncn = std::max(P.max_ncn, ncn);
-        P.Kinv.insert(P.Kinv.end(), In.Kinv.begin(), In.Kinv.end());
         // per interface dof
         const int64_t ngam = (int64_t)In.gamma.size();
         std::vector<int> sa(ngam, -1), sb(ngam, -1);
@@ -1281,30 +1280,12 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
             // a block can be copied whole by a 1D bulk copy
             auto pad4 = [](int64_t n) { return (n + 3) & ~(int64_t)3; };
             const int64_t nS = (int64_t)S.ng * S.ng, nP = (int64_t)S.m * S.ng;
-            // S and F are symmetric in exact arithmetic; store them exactly
-            // symmetric (mean of the two rounded triangles) so that one
-            // triangle describes each, as the device keeps it
-            symmetrize(S.S, S.ng);
-            symmetrize(S.F, S.ng);
-            P.S.insert(P.S.end(), S.S.begin(), S.S.end());
-            P.S.resize(oS + pad4(nS), 0.0);
+            // the operator blocks are copied after this loop, in parallel, at
+            // these offsets
             oS += pad4(nS);
-            P.P64.insert(P.P64.end(), S.PsiT.begin(), S.PsiT.end());
-            P.P64.resize(oP + pad4(nP), 0.0);
-            if (opt.precision == BDDC_PREC_FP32) {
-                for (double v : S.F) P.F32.push_back((float)v);
-                P.F32.resize(oF + pad4(nS), 0.0f);
-                for (double v : S.PsiT) P.P32.push_back((float)v);
-                P.P32.resize(oP + pad4(nP), 0.0f);
-            } else {
-                P.F64.insert(P.F64.end(), S.F.begin(), S.F.end());
-                P.F64.resize(oF + pad4(nS), 0.0);
-            }
             oF += pad4(nS);
             oP += pad4(nP);
-            P.Gpre.insert(P.Gpre.end(), S.GpreT.begin(), S.GpreT.end());
             oGpre += (int64_t)S.nc * S.ng;
-            if (!P.dev_Gpost) P.Gpost.insert(P.Gpost.end(), S.GpostT.begin(), S.GpostT.end());
             oGpost += (int64_t)(S.ng + S.nc) * (S.ni + S.nc);
             for (int k = 0; k < S.ng; ++k) {
                 const int g = S.gidx[k];
@@ -1381,6 +1362,45 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         for (int c = 0; c < In.n_cf; ++c) { P.c_slot_a.push_back(ca[c]); P.c_slot_b.push_back(cb[c]); }
         goff += ngam; coff += ncn; kinv_off += (int64_t)In.Kinv.size(); s_glob += In.N;
         face_off += In.geo.n_faces; cell_off += In.geo.n_cells;
+    }
+    // the operator blocks and coarse inverses, copied in parallel into arrays
+    // sized once (zero padding included).  S and F are symmetric in exact
+    // arithmetic; they are stored exactly symmetric (mean of the two rounded
+    // triangles) so that one triangle describes each.
+    {
+        std::vector<std::pair<int, int>> subs;
+        for (int b = 0; b < n_inst; ++b)
+            for (int q = 0; q < I[b].N; ++q) subs.emplace_back(b, q);
+        const bool fp32 = opt.precision == BDDC_PREC_FP32;
+        P.S.assign((size_t)oS, 0.0);
+        P.P64.assign((size_t)oP, 0.0);
+        if (fp32) {
+            P.F32.assign((size_t)oF, 0.0f);
+            P.P32.assign((size_t)oP, 0.0f);
+        } else {
+            P.F64.assign((size_t)oF, 0.0);
+        }
+        P.Gpre.assign((size_t)oGpre, 0.0);
+        if (!P.dev_Gpost) P.Gpost.assign((size_t)oGpost, 0.0);
+        parallel_for((int64_t)subs.size(), nthreads, [&](int64_t g) {
+            Sub& S = I[subs[g].first].subs[subs[g].second];
+            symmetrize(S.S, S.ng);
+            symmetrize(S.F, S.ng);
+            std::copy(S.S.begin(), S.S.end(), P.S.begin() + P.off_S[g]);
+            std::copy(S.PsiT.begin(), S.PsiT.end(), P.P64.begin() + P.off_P[g]);
+            if (fp32) {
+                std::transform(S.F.begin(), S.F.end(), P.F32.begin() + P.off_F[g], [](double v) { return (float)v; });
+                std::transform(S.PsiT.begin(), S.PsiT.end(), P.P32.begin() + P.off_P[g], [](double v) { return (float)v; });
+            } else {
+                std::copy(S.F.begin(), S.F.end(), P.F64.begin() + P.off_F[g]);
+            }
+            std::copy(S.GpreT.begin(), S.GpreT.end(), P.Gpre.begin() + P.off_Gpre[g]);
+            if (!P.dev_Gpost) std::copy(S.GpostT.begin(), S.GpostT.end(), P.Gpost.begin() + P.off_Gpost[g]);
+        });
+        P.Kinv.assign((size_t)kinv_off, 0.0);
+        parallel_for(n_inst, nthreads, [&](int64_t b) {
+            std::copy(I[b].Kinv.begin(), I[b].Kinv.end(), P.Kinv.begin() + P.inst_kinv_off[b]);
+        });
     }
     // slot partner (the other copy of the same interface dof)
     P.slot_partner.assign(slot, -1);
