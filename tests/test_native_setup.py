@@ -212,3 +212,17 @@ def test_setup_maps_are_accurate_at_high_contrast():
     flux, pres, _, _, _ = emulate_solve(Packed(hs), pb.f, pb.bc_value, 1e-12)
     assert np.linalg.norm(flux - fd) <= 1e-10 * np.linalg.norm(fd)
     assert np.linalg.norm(pres - pd) <= 1e-10 * np.linalg.norm(pd)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_packed_setup_does_not_depend_on_thread_count(precision):
+    """The setup packs the operator blocks and coarse inverses in parallel
+    (one task per subdomain and instance, at offsets fixed before the copy):
+    every exported array is bitwise the same for 1 and 8 host threads."""
+    pbs = [make_config("c1"), CASES["irregular2d"](), CASES["tiny3d"]()]
+    one = bddc.HostSetup(pbs, bddc.default_options(tau=4.0, precision=precision, n_threads=1))
+    many = bddc.HostSetup(pbs, bddc.default_options(tau=4.0, precision=precision, n_threads=8))
+    for name in ("S", "F", "P", "P64", "Gpre", "Gpost", "Kinv", "off_S", "off_F", "off_P", "off_Gpre",
+                 "off_Gpost", "slot_g", "slot_w", "cslot_c", "inst_kinv_off"):
+        a, b = one.get(name), many.get(name)
+        assert a.dtype == b.dtype and np.array_equal(a, b), name
