@@ -173,6 +173,9 @@ def test_server_without_gpu_and_invalid_arguments():
     assert lib.bddc_server_create(C.byref(o), 0, 4, C.byref(out)) == bddc.BDDC_E_INVALID_ARG
     assert lib.bddc_server_create(C.byref(o), 1 << 30, 0, C.byref(out)) == bddc.BDDC_E_INVALID_ARG
     assert lib.bddc_server_create(C.byref(o), 1 << 30, 4, None) == bddc.BDDC_E_INVALID_ARG
+    # the full-space operator form needs the FP64 path
+    bad = bddc.default_options(formulation=bddc.BDDC_FORM_FULL, precision=bddc.BDDC_PREC_FP32)
+    assert lib.bddc_server_create(C.byref(bad), 1 << 30, 4, C.byref(out)) == bddc.BDDC_E_INVALID_ARG
     t = C.c_uint64()
     assert lib.bddc_submit(None, None, None, None, 1e-8, C.byref(t)) == bddc.BDDC_E_INVALID_ARG
     assert lib.bddc_poll(None, 1, None, None, None, None, None) == bddc.BDDC_E_INVALID_ARG
