@@ -966,8 +966,7 @@ SetupResult coarse_dense(Inst& I, const std::vector<CoarseElement>& el) {
     std::vector<int> piv;
     if (!lu(n, K.data(), piv)) return {BDDC_E_SETUP, "singular coarse problem"};
     std::vector<double> X((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) X[(size_t)i * n + i] = 1.0;
-    lu_solve(n, K.data(), piv, X.data(), n);
+    lu_inverse(n, K.data(), piv, X.data());
     const int ncn = ncf + N;
     I.Kinv.assign((size_t)ncn * ncn, 0.0);
     for (int a = 0; a < ncn; ++a)

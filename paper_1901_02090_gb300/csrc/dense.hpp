@@ -115,6 +115,45 @@ inline void lu_solve(int n, const double* LU, const std::vector<int>& piv, doubl
     }
 }
 
+// Inverse from the LU factors, X = A^{-1} (n x n row-major): the operations
+// of lu_solve on the identity without the products with the structural zeros
+// of P I.  With the right-hand sides taken in pivot order the forward sweep
+// solves with an identity, so row k of L^{-1} has entries in its first k + 1
+// columns only (n^3 / 6 multiply-adds instead of n^3 / 2); every entry gets
+// the same sequence of operations, so the result is bitwise that of
+// lu_solve.
+inline void lu_inverse(int n, const double* LU, const std::vector<int>& piv, double* X) {
+    std::vector<int> perm(n), pos(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int k = 0; k < n; ++k)
+        if (piv[k] != k) std::swap(perm[k], perm[piv[k]]);
+    for (int i = 0; i < n; ++i) pos[perm[i]] = i;  // the row of P I holding column c's 1
+    std::vector<double> W((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double* wi = W.data() + (size_t)i * n;
+        wi[i] = 1.0;
+        for (int k = 0; k < i; ++k) {
+            const double l = LU[(size_t)i * n + k];
+            if (l == 0.0) continue;
+            const double* wk = W.data() + (size_t)k * n;
+            for (int c = 0; c <= k; ++c) wi[c] -= l * wk[c];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double* wi = W.data() + (size_t)i * n;
+        for (int k = i + 1; k < n; ++k) {
+            const double u = LU[(size_t)i * n + k];
+            if (u == 0.0) continue;
+            const double* wk = W.data() + (size_t)k * n;
+            for (int c = 0; c < n; ++c) wi[c] -= u * wk[c];
+        }
+        const double d = 1.0 / LU[(size_t)i * n + i];
+        for (int c = 0; c < n; ++c) wi[c] *= d;
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) X[(size_t)r * n + c] = W[(size_t)r * n + pos[c]];
+}
+
 // Orthonormal basis of the orthogonal complement of the row space of the
 // m x n matrix C (rows assumed linearly independent), by Householder QR of
 // C^T.  Returns Z as n x (n - m) row-major.
