@@ -229,3 +229,20 @@ def test_packed_setup_does_not_depend_on_thread_count(precision):
                  "off_Gpost", "slot_g", "slot_w", "cslot_c", "inst_kinv_off"):
         a, b = one.get(name), many.get(name)
         assert a.dtype == b.dtype and np.array_equal(a, b), name
+
+
+def test_incompatible_pure_flux_data_solve_the_compatible_part():
+    """No pressure face and a net source: the bordered coarse problem removes
+    the mean source; the flux equations converge and every cell's mass
+    residual is the mean source per cell (what true_relres reports)."""
+    from oracle.discretization import Discretization, residuals
+    pb = make_config("c1")
+    pb.bc_type, pb.bc_value = no_flow_bc(pb.grid)
+    pb.f = np.zeros(pb.grid.n_cells)
+    pb.f[3] = 2.0 / pb.grid.cell_volume
+    hs = bddc.HostSetup([pb], bddc.default_options(tau=4.0))
+    flux, pres, its, _, _ = emulate_solve(Packed(hs), pb.f, pb.bc_value, 1e-10)
+    r1, r2 = residuals(Discretization(pb), flux, pres)
+    assert np.abs(r1).max() <= 1e-9 * np.abs(flux).max()
+    mean_source = pb.f.sum() * pb.grid.cell_volume / pb.grid.n_cells
+    assert np.allclose(np.abs(r2), abs(mean_source), rtol=1e-8)
