@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "bddc_internal.hpp"
+#include "bddc_trace.hpp"
 
 namespace {
 
@@ -154,6 +155,7 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
         r->t_setup = t0;
         r->info.queue_ms = ms_between(r->t_submit, t0);
     }
+    bddc::TraceStage stage("bddc_server: batch setup");
     std::vector<bddc_instance> inst;
     for (auto& r : reqs) inst.push_back(r->instance());
     bddc::Packed P;
@@ -207,6 +209,7 @@ void setup_batch(bddc_server* s, std::vector<ReqPtr> reqs) {
         s->peak = std::max(s->peak, s->in_use);
     }
     bddc_handle* h = nullptr;
+    stage.next("bddc_server: upload");
     const int rc = bddc::setup_from_packed(n, s->opt, s->stream, std::move(P), &h);
     if (rc) {
         {
@@ -276,6 +279,7 @@ void solve_batch(bddc_server* s, Batch& b) {
     }
     std::vector<double> flux((size_t)face_off[n]), pres((size_t)cell_off[n]);
     std::vector<int> its(n, 0);
+    bddc::TraceStage stage("bddc_server: batch solve");
     const int rc = bddc_solve(b.h, f.data(), bc.data(), b.tol, flux.data(), pres.data(), its.data());
     std::vector<int> status(n, rc);
     for (int i = 0; i < n; ++i) {

@@ -42,6 +42,7 @@
 #include <tuple>
 
 #include "bddc_internal.hpp"
+#include "bddc_trace.hpp"
 #include "dense.hpp"
 
 namespace bddc {
@@ -1075,6 +1076,7 @@ SetupResult device_local_maps(std::vector<Inst>& I, const std::vector<std::pair<
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P,
                       LocalMapsDevice device, FaceEigenDevice eig_device) {
     const int nthreads = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    TraceStage stage("bddc_setup: instances and topology");
     std::vector<Inst> I(n_inst);
     {
         std::vector<SetupResult> rr(n_inst);
@@ -1097,6 +1099,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     };
     std::shared_ptr<double> dev_gpost;
     int64_t dev_gpost_count = 0;
+    stage.next("bddc_setup: local maps");
     if (device) {
         SetupResult r = device_local_maps(I, tasks, opt.pressure_scaling != 0, nthreads, device, dev_gpost,
                                           dev_gpost_count);
@@ -1109,6 +1112,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         });
         if (err.code) return err;
     }
+    stage.next("bddc_setup: weights and constraints (Algorithm 3)");
     for (int b = 0; b < n_inst; ++b) weights(I[b], opt.scaling);
     const bool adaptive = opt.tau > 0 && std::isfinite(opt.tau);
     {
@@ -1204,6 +1208,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         }
     }
     for (int b = 0; b < n_inst; ++b) gather_constraints(I[b]);
+    stage.next("bddc_setup: correction maps");
     parallel_for((int64_t)tasks.size(), nthreads, [&](int64_t t) {
         auto [b, s] = tasks[t];
         SetupResult r = correction_maps(I[b].subs[s]);
@@ -1211,6 +1216,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     });
     if (err.code) return err;
     // coarse solver: dense inverse, or the sparse factor for large coarse problems
+    stage.next("bddc_setup: coarse solver");
     int max_ncn = 0;
     for (int b = 0; b < n_inst; ++b) max_ncn = std::max(max_ncn, I[b].n_cf + I[b].N);
     const bool sparse = opt.coarse_solver == BDDC_COARSE_SPARSE ||
@@ -1225,6 +1231,7 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
         if (cres[b].code) { cres[b].msg = "instance " + std::to_string(b) + ": " + cres[b].msg; return cres[b]; }
 
     // ---- pack -----------------------------------------------------------------
+    stage.next("bddc_setup: pack");
     P = Packed();
     P.precision = opt.precision;
     P.dev_Gpost = dev_gpost;  // set: G_post is on the device and P.Gpost stays empty
