@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -43,6 +44,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--single-solves", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests of the serving stream (0: skip it)")
     ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrival rate of the stream (1/s)")
@@ -90,11 +92,13 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, directory=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bddc_clocks_{os.getpid()}.csv"
+        # the raw samples: in the directory given by --clocks-dir (kept for
+        # inspection), else a temporary file
+        d = directory or tempfile.gettempdir()
+        self.path = os.path.join(d, f"bddc_clocks_{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -355,7 +359,7 @@ def main():
             bad = [(i, h.stats(i).status, h.stats(i).iterations, h.stats(i).relres) for i in range(B)
                    if h.stats(i).status != bddc.BDDC_OK]
             raise RuntimeError(f"batched solve failed (rc={rc}): instances {bad[:8]}")
-    clocks = Clocks(local_rank)
+    clocks = Clocks(local_rank, args.clocks_dir)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
