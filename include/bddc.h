@@ -63,6 +63,14 @@ extern "C" {
 #define BDDC_PREC_FP64 0
 #define BDDC_PREC_FP32 1
 
+/* Weights of the averaging operator E (Sec. 3), one value per side of each
+ * face Gamma^{ij} (1 on pressure faces): multiplicity 1/2; stiffness the
+ * face's share of the diagonals of the local a-form matrices,
+ * sum_F A^i_ee / sum_F (A^i_ee + A^j_ee), which for RT0 is the rho-scaling
+ * k_i^-1 / (k_i^-1 + k_j^-1) when k jumps across subdomain interfaces only
+ * (Sec. 5).  The weights are constant along each face because the net-flux
+ * constraints keep the Step-2 flux conservative only then (Sec. 3, Remark
+ * "scaling"). */
 #define BDDC_SCALING_MULTIPLICITY 0
 #define BDDC_SCALING_STIFFNESS 1
 
@@ -196,16 +204,23 @@ int bddc_apply_preconditioner(bddc_handle* h, const double* r, double* z, double
 /* Subassembled operator apply from caller-owned device data, the kernel of
  * eqs. (corr-reduced-1/2) without a handle: q = sum_i R_i^T S^i R_i u.
  *   n_sub       : number of subdomains
- *   ng          : n_sub local interface sizes (each <= 1024)
- *   slot_offset : n_sub + 1 prefix offsets of the local slots (sum of ng)
+ *   ng          : n_sub local interface sizes (each 0..1024)
+ *   slot_offset : n_sub + 1 prefix offsets of the local slots: slot_offset[0]
+ *                 = 0 and slot_offset[s + 1] - slot_offset[s] = ng[s]
  *   S_offset    : n_sub offsets (in doubles) of each S^i in S
  *   S           : the dense symmetric S^i, row-major, ng x ng each
- *   gidx        : slot -> global interface index
+ *   gidx        : slot -> global interface index (0..n_interface-1)
  *   partner     : slot -> slot of the other copy of the same dof, or -1
  *   u           : n_interface input
- *   q           : n_interface output (every entry is written)
+ *   q           : n_interface output (every entry with a slot is written)
  *   slot_scratch: caller-owned scratch of slot_offset[n_sub] doubles
- * Device pointers; stream is a cudaStream_t or NULL. */
+ * Device pointers; stream is a cudaStream_t or NULL.  ng and slot_offset are
+ * read back on `stream` (the call waits for the work queued there before
+ * it) and checked on the host: sizes outside 0..1024 or offsets that are not
+ * the prefix sums of ng give BDDC_E_INVALID_ARG before any launch (message
+ * from bddc_last_error(NULL)).  The kernels skip any slot, partner or
+ * interface index outside its buffer, so bad index tables give wrong values
+ * but no access outside u, q and the scratch. */
 int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset,
                             const int64_t* S_offset, const double* S, const int* gidx,
                             const int* partner, int64_t n_interface, const double* u,
@@ -216,16 +231,21 @@ int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset
  * cannot call cudaMalloc: code running where the device allocator is
  * forbidden or already reserved (inside a caller's memory pool or arena
  * that owns all device memory, in real-time or safety-certified loops that
- * allow no allocation after start-up).  This entry point takes the same
- * inputs and output but no scratch argument: its per-slot scratch is a fixed
- * array in the library's device memory, BDDC_NOALLOC_MAX_SLOTS doubles
+ * allow no device allocation after start-up).  This entry point takes the
+ * same inputs and output but no scratch argument: its per-slot scratch is a
+ * fixed array in the library's device memory, BDDC_NOALLOC_MAX_SLOTS doubles
  * (4 MiB), held by every GPU that loads the library until the process
- * exits.  It allocates nothing and calls no cudaMalloc or cudaFree.
- *   - slot_offset[n_sub] larger than BDDC_NOALLOC_MAX_SLOTS is rejected with
- *     BDDC_E_INVALID_ARG (message from bddc_last_error(NULL));
+ * exits.  It makes no device allocation: no cudaMalloc, cudaFree or
+ * allocating library routine (its host-side checks use small host buffers).
+ *   - ng and slot_offset are read back on `stream` and checked as for
+ *     bddc_subassembled_apply; slot_offset[n_sub] larger than
+ *     BDDC_NOALLOC_MAX_SLOTS is rejected with BDDC_E_INVALID_ARG (message
+ *     from bddc_last_error(NULL)); the kernels never address the array past
+ *     slot_offset[n_sub], whatever the index tables hold;
+ *   - the read-back synchronises `stream`, so the call cannot be captured in
+ *     a CUDA graph;
  *   - the first call on a device looks up the array's device address on the
- *     current device (once per device); make that first call before any
- *     stream capture;
+ *     current device (once per device);
  *   - every call on a device shares the one array; it needs no clearing
  *     (each call writes every slot it reads), and calls whose kernels
  *     overlap on the GPU (different streams, or another host thread) race on

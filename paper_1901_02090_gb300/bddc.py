@@ -281,7 +281,7 @@ def subassembled_apply(n_sub, ng, slot_offset, S_offset, S, gidx, partner, n_int
                                      _ptr(gidx), _ptr(partner), int(n_interface), _ptr(u), _ptr(q),
                                      _ptr(slot_scratch), None if stream is None else C.c_void_p(int(stream)))
     if rc != BDDC_OK:
-        raise BDDCError(rc)
+        raise BDDCError(rc, lib.bddc_last_error(None).decode())
 
 
 NOALLOC_MAX_SLOTS = 1 << 19

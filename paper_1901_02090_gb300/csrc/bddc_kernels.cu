@@ -1442,23 +1442,47 @@ __global__ void k_pairs(int64_t n, const double* src, float2* dst) {
     }
 }
 
-// raw subassembled apply (no handle)
+// raw subassembled apply (no handle), from caller-owned index tables: the
+// host has checked the sizes and the slot offsets; every index read from a
+// caller table is also checked here against the buffer it addresses (slots
+// against n_slots, interface indices against n_in), and an access outside
+// is skipped, so bad table entries can give wrong values but never reach
+// memory outside the caller's arrays and the scratch
 __global__ void __launch_bounds__(128) k_subassembled_local(int n_sub, const int* ng_arr, const int64_t* slot_off,
                                                             const int64_t* S_off, const double* S, const int* gidx,
-                                                            const double* u, double* scratch) {
+                                                            const double* u, double* scratch, int64_t n_slots,
+                                                            int64_t n_in) {
     __shared__ double xs[1024];
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
         const int ng = ng_arr[s];
         const int64_t so = slot_off[s];
-        for (int k = threadIdx.x; k < ng; k += blockDim.x) xs[k] = u[gidx[so + k]];
+        for (int k = threadIdx.x; k < ng; k += blockDim.x) {
+            const int64_t q = so + k;
+            const int g = (q >= 0 && q < n_slots) ? gidx[q] : -1;
+            xs[k] = (g >= 0 && g < n_in) ? u[g] : 0.0;
+        }
         __syncthreads();
         const double* M = S + S_off[s];
         for (int k = threadIdx.x; k < ng; k += blockDim.x) {
             double acc = 0.0;
             for (int j = 0; j < ng; ++j) acc = fma(__ldg(M + (int64_t)j * ng + k), xs[j], acc);
-            scratch[so + k] = acc;
+            const int64_t q = so + k;
+            if (q >= 0 && q < n_slots) scratch[q] = acc;
         }
         __syncthreads();
+    }
+}
+
+// assembly of the raw apply: k_assemble with the partner slot and the
+// output index checked against their buffers
+__global__ void k_assemble_checked(int64_t n_slots, const double* loc, const int* slot_g, const int* partner,
+                                   int64_t n_out, double* out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_slots; q += (int64_t)gridDim.x * blockDim.x) {
+        const int pt = partner[q];
+        if (pt >= 0 && pt < q) continue;
+        const int g = slot_g[q];
+        if (g < 0 || g >= n_out || pt >= n_slots) continue;
+        out[g] = loc[q] + (pt >= 0 ? loc[pt] : 0.0);
     }
 }
 
@@ -2203,24 +2227,82 @@ int bddc_apply_preconditioner(bddc_handle* h, const double* r, double* z, double
     return e == cudaSuccess ? BDDC_OK : set_err(h, BDDC_E_CUDA, cudaGetErrorString(e));
 }
 
+}  // extern "C"
+
+namespace {
+// Sizes of a raw subassembled apply, read on the caller's stream (so that
+// work queued there before the call, which may write the tables, is
+// finished) and validated: every local size 0..1024, slot_offset[0] = 0 and
+// slot_offset[s + 1] - slot_offset[s] = ng[s] (consecutive, non-overlapping
+// slot ranges), the total at most max_slots.  Returns BDDC_OK with the
+// total in *n_slots, or an error code with the message in *msg.
+int raw_apply_sizes(int n_sub, const int* ng, const int64_t* slot_offset, cudaStream_t st, int64_t max_slots,
+                    int64_t* n_slots, std::string* msg) {
+    std::vector<int> hng((size_t)n_sub);
+    std::vector<int64_t> hoff((size_t)n_sub + 1);
+    cudaError_t e = cudaMemcpyAsync(hng.data(), ng, sizeof(int) * (size_t)n_sub, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hoff.data(), slot_offset, sizeof(int64_t) * ((size_t)n_sub + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *msg = std::string("reading the sizes: ") + cudaGetErrorString(e);
+        return BDDC_E_CUDA;
+    }
+    if (hoff[0] != 0) {
+        *msg = "slot_offset[0] must be 0";
+        return BDDC_E_INVALID_ARG;
+    }
+    for (int s = 0; s < n_sub; ++s) {
+        if (hng[s] < 0 || hng[s] > 1024) {
+            *msg = "local interface size " + std::to_string(hng[s]) + " of subdomain " + std::to_string(s) +
+                   " is outside 0..1024";
+            return BDDC_E_INVALID_ARG;
+        }
+        if (hoff[s + 1] - hoff[s] != hng[s]) {
+            *msg = "slot_offset is not the prefix sum of ng at subdomain " + std::to_string(s);
+            return BDDC_E_INVALID_ARG;
+        }
+    }
+    *n_slots = hoff[n_sub];
+    if (*n_slots > max_slots) {
+        *msg = std::to_string(*n_slots) + " local slots exceed the fixed scratch of " + std::to_string(max_slots) +
+               " doubles; use bddc_subassembled_apply with caller scratch";
+        return BDDC_E_INVALID_ARG;
+    }
+    return BDDC_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset, const int64_t* S_offset,
                             const double* S, const int* gidx, const int* partner, int64_t n_interface,
                             const double* u, double* q, double* slot_scratch, void* stream) {
+    g_setup_err.clear();
     if (n_sub <= 0 || !ng || !slot_offset || !S_offset || !S || !gidx || !partner || !u || !q || !slot_scratch ||
-        n_interface <= 0)
+        n_interface <= 0) {
+        g_setup_err = "bddc_subassembled_apply: null pointer or non-positive size";
         return BDDC_E_INVALID_ARG;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int64_t n_slots = 0;
-    if (cudaMemcpy(&n_slots, slot_offset + n_sub, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return BDDC_E_CUDA;
-    std::vector<int> hng(n_sub);
-    if (cudaMemcpy(hng.data(), ng, sizeof(int) * n_sub, cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
-    for (int v : hng)
-        if (v < 0 || v > 1024) return BDDC_E_INVALID_ARG;
+    std::string msg;
+    const int rc = raw_apply_sizes(n_sub, ng, slot_offset, st, INT32_MAX, &n_slots, &msg);
+    if (rc) {
+        g_setup_err = "bddc_subassembled_apply: " + msg;
+        return rc;
+    }
+    cudaGetLastError();  // an earlier, unrelated launch error is not this call's
     k_subassembled_local<<<std::min(n_sub, 4096), 128, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u,
-                                                                slot_scratch);
-    k_assemble<<<(int)std::min<int64_t>((n_slots + 255) / 256, 4096), 256, 0, st>>>(n_slots, slot_scratch, gidx, partner, q);
-    return cudaGetLastError() == cudaSuccess ? BDDC_OK : BDDC_E_CUDA;
+                                                                slot_scratch, n_slots, n_interface);
+    k_assemble_checked<<<(int)std::max<int64_t>(1, std::min<int64_t>((n_slots + 255) / 256, 4096)), 256, 0, st>>>(
+        n_slots, slot_scratch, gidx, partner, n_interface, q);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_setup_err = std::string("bddc_subassembled_apply: launch: ") + cudaGetErrorString(e);
+        return BDDC_E_CUDA;
+    }
+    return BDDC_OK;
 }
 
 }  // extern "C"
@@ -2270,28 +2352,29 @@ extern "C" int bddc_subassembled_apply_noalloc(int n_sub, const int* ng, const i
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int64_t n_slots = 0;
-    if (cudaMemcpy(&n_slots, slot_offset + n_sub, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return BDDC_E_CUDA;
-    if (n_slots < 0 || n_slots > (int64_t)BDDC_NOALLOC_MAX_SLOTS) {
-        g_setup_err = "bddc_subassembled_apply_noalloc: " + std::to_string(n_slots) +
-                      " local slots exceed the fixed scratch of " + std::to_string(BDDC_NOALLOC_MAX_SLOTS) +
-                      " doubles; use bddc_subassembled_apply with caller scratch";
-        return BDDC_E_INVALID_ARG;
+    std::string msg;
+    int rc = raw_apply_sizes(n_sub, ng, slot_offset, st, (int64_t)BDDC_NOALLOC_MAX_SLOTS, &n_slots, &msg);
+    if (rc) {
+        g_setup_err = "bddc_subassembled_apply_noalloc: " + msg;
+        return rc;
     }
-    std::vector<int> hng(n_sub);
-    if (cudaMemcpy(hng.data(), ng, sizeof(int) * n_sub, cudaMemcpyDeviceToHost) != cudaSuccess) return BDDC_E_CUDA;
-    for (int v : hng)
-        if (v < 0 || v > 1024) {
-            g_setup_err = "bddc_subassembled_apply_noalloc: a local interface size exceeds 1024";
-            return BDDC_E_INVALID_ARG;
-        }
     double* scratch = nullptr;
-    const int rc = noalloc_scratch(&scratch);
+    rc = noalloc_scratch(&scratch);
     if (rc) {
         g_setup_err = "bddc_subassembled_apply_noalloc: cudaGetSymbolAddress failed";
         return rc;
     }
-    k_subassembled_local<<<std::min(n_sub, 4096), 128, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u, scratch);
-    k_assemble<<<(int)std::min<int64_t>((n_slots + 255) / 256, 4096), 256, 0, st>>>(n_slots, scratch, gidx, partner, q);
-    return cudaGetLastError() == cudaSuccess ? BDDC_OK : BDDC_E_CUDA;
+    cudaGetLastError();  // an earlier, unrelated launch error is not this call's
+    // the kernels' index checks use n_slots (at most the array's size), so
+    // no access leaves the fixed array, whatever the caller's tables hold
+    k_subassembled_local<<<std::min(n_sub, 4096), 128, 0, st>>>(n_sub, ng, slot_offset, S_offset, S, gidx, u, scratch,
+                                                                n_slots, n_interface);
+    k_assemble_checked<<<(int)std::max<int64_t>(1, std::min<int64_t>((n_slots + 255) / 256, 4096)), 256, 0, st>>>(
+        n_slots, scratch, gidx, partner, n_interface, q);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_setup_err = std::string("bddc_subassembled_apply_noalloc: launch: ") + cudaGetErrorString(e);
+        return BDDC_E_CUDA;
+    }
+    return BDDC_OK;
 }

@@ -729,19 +729,43 @@ void gather_constraints(Inst& I) {
     }
 }
 
+// Weights of the averaging operator E (Sec. 3), one value per face Gamma^{ij}
+// and side: 1/2 (multiplicity), or the face's share of the local diagonals
+// sum_F A^i_ee / sum_F (A^i_ee + A^j_ee) (stiffness, Sec. 5); 1 on pressure
+// faces.  The Remark "scaling" of Sec. 3: the net-flux constraints keep u*
+// conservative only if the weights do not vary along a face; where k jumps
+// across the subdomain boundaries only, the per-dof ratios are constant along
+// each face and equal these (the rho-scaling of RT0).
 void weights(Inst& I, int scaling) {
-    // total diagonal per interface dof over the subdomains sharing it
-    std::vector<double> tot(I.gamma.size(), 0.0);
-    std::vector<int> mult(I.gamma.size(), 0);
-    for (Sub& S : I.subs)
-        for (int k = 0; k < S.ng; ++k) { tot[S.gidx[k]] += S.diagA[k]; mult[S.gidx[k]]++; }
-    for (Sub& S : I.subs) {
-        S.w.resize(S.ng);
-        for (int k = 0; k < S.ng; ++k) {
-            const int g = S.gidx[k];
-            if (mult[g] == 1) S.w[k] = 1.0;
-            else if (scaling == BDDC_SCALING_STIFFNESS) S.w[k] = S.diagA[k] / tot[g];
-            else S.w[k] = 1.0 / mult[g];
+    // slot of every interface index in each of its (at most two) subdomains
+    std::vector<int> sa(I.gamma.size(), -1), sb(I.gamma.size(), -1);
+    for (int s = 0; s < (int)I.subs.size(); ++s) {
+        Sub& S = I.subs[s];
+        S.w.assign(S.ng, 1.0);
+        for (int k = 0; k < S.ng; ++k) (sa[S.gidx[k]] < 0 ? sa : sb)[S.gidx[k]] = k;
+    }
+    for (const Face& F : I.faces) {
+        if (F.dir) continue;
+        Sub& Si = I.subs[F.i];
+        Sub& Sj = I.subs[F.j];
+        // the slot of dof g in subdomain X: whichever of sa/sb maps back to g there
+        auto slot = [&](const Sub& X, int g) {
+            const int a = sa[g];
+            return (a >= 0 && a < X.ng && X.gidx[a] == g) ? a : sb[g];
+        };
+        double wi = 0.5, wj = 0.5;
+        if (scaling == BDDC_SCALING_STIFFNESS) {
+            double ai = 0.0, aj = 0.0;
+            for (int g : F.gidx) {
+                ai += Si.diagA[slot(Si, g)];
+                aj += Sj.diagA[slot(Sj, g)];
+            }
+            wi = ai / (ai + aj);
+            wj = aj / (ai + aj);
+        }
+        for (int g : F.gidx) {
+            Si.w[slot(Si, g)] = wi;
+            Sj.w[slot(Sj, g)] = wj;
         }
     }
 }

@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "Grid", "Problem", "n_faces", "face_axis_counts", "box_partition",
     "irregular_box_partition", "lognormal_iid", "gaussian_field",
-    "channelized_2d", "layered_3d", "pressure_drop_bc",
+    "channelized_2d", "layered_3d", "subdomain_constant", "pressure_drop_bc",
     "directional_pressure_bc", "no_flow_bc", "corner_wells", "make_config",
 ]
 
@@ -254,6 +254,18 @@ def layered_3d(grid: Grid, seed: int) -> np.ndarray:
                 p["phi"] += rng.normal(0.0, 0.05)
             _channel_layer(nx, ny, rng, layer, drift=params)
     return 10.0 ** log10k.reshape(-1)
+
+
+def subdomain_constant(partition: np.ndarray, seed: int, lo10: float = -3.0, hi10: float = 3.0,
+                       n_comp: int = 1) -> np.ndarray:
+    """Permeability constant inside every subdomain (jumps aligned with the
+    subdomain interfaces, the setting of the paper's stiffness-scaling test):
+    log10 k ~ U[lo10, hi10] per subdomain (and per axis when n_comp > 1)."""
+    rng = np.random.default_rng(seed)
+    n_sub = int(partition.max()) + 1
+    vals = 10.0 ** rng.uniform(lo10, hi10, (n_sub, n_comp))
+    k = vals[partition]
+    return np.ascontiguousarray(k[:, 0] if n_comp == 1 else k)
 
 
 def make_config(name: str, seed: int | None = None) -> Problem:

@@ -32,8 +32,8 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
 
 
-def gpu_solve(bddc, pbs, tol, tau=None, precision=0, device_io=True, maxit=5000, check=True):
-    opt = bddc.default_options(tau=tau or 0.0, precision=precision, maxit=maxit)
+def gpu_solve(bddc, pbs, tol, tau=None, precision=0, device_io=True, maxit=5000, check=True, scaling=0):
+    opt = bddc.default_options(tau=tau or 0.0, precision=precision, maxit=maxit, scaling=scaling)
     stream = torch.cuda.current_stream().cuda_stream
     h = bddc.setup(pbs, opt, stream=stream)
     f = np.concatenate([pb.f for pb in pbs])
@@ -114,6 +114,60 @@ def test_fp64_solve_matches_oracle(bddc, case, tau):
     if tau is not None:
         assert np.isclose(st[0].omega_tilde, o.omega_tilde, rtol=1e-8)
         assert st[0].n_coarse == o.n_coarse
+
+
+@pytest.mark.parametrize("case", ["c1", "tiny3d", "irregular3d_anisotropic"])
+@pytest.mark.parametrize("tau", [None, 4.0])
+def test_stiffness_scaling_matches_oracle(bddc, case, tau):
+    """BDDC_SCALING_STIFFNESS (weights of E per face side, Sec. 3 Remark
+    "scaling" and Sec. 5): the FP64 path against the oracle's stiffness-
+    scaled solve at tol 1e-8 and 1e-12, with omega-tilde and the coarse size
+    of the w-weighted face eigenproblems; the mixed path within its bound."""
+    pb = CASES[case]()
+    o = BDDCOracle(pb, tau=tau, scaling="stiffness")
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, tau, scaling=bddc.BDDC_SCALING_STIFFNESS)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= max(FP64_REL, 1e-8 * ref.kappa)
+    assert _rel(pres, ref.pressure) <= max(FP64_REL, 1e-8 * ref.kappa)
+    assert abs(st[0].kappa - ref.kappa) <= 0.02 * ref.kappa
+    if tau is not None:
+        assert np.isclose(st[0].omega_tilde, o.omega_tilde, rtol=1e-8)
+        assert st[0].n_coarse == o.n_coarse
+    flux32, pres32, _, _, _ = gpu_solve(bddc, [pb], 1e-8, tau, precision=bddc.BDDC_PREC_FP32,
+                                        scaling=bddc.BDDC_SCALING_STIFFNESS)
+    assert _rel(flux32, ref.flux) <= MIXED_REL and _rel(pres32, ref.pressure) <= MIXED_REL
+    ref = o.solve(tol=1e-12)
+    flux, pres, _, _, _ = gpu_solve(bddc, [pb], 1e-12, tau, scaling=bddc.BDDC_SCALING_STIFFNESS)
+    assert _rel(flux, ref.flux) <= CONVERGED_REL
+    assert _rel(pres, ref.pressure) <= CONVERGED_REL
+
+
+@pytest.mark.parametrize("field", ["channelized", "aligned_jumps"])
+def test_stiffness_scaling_60x220(bddc, field):
+    """The 60 x 220 grid (6 x 22 subdomains) with stiffness scaling, both
+    precisions, adaptive tau = 10: the channelized field (jumps across and
+    along the interfaces) and a field constant per subdomain (jumps aligned
+    with the interfaces, up to 1e6, the paper's stiffness-scaling case)."""
+    from synth.problems import subdomain_constant
+    from oracle.discretization import residuals
+    pb = make_config("c2", seed=2093)
+    if field == "aligned_jumps":
+        pb.perm = subdomain_constant(pb.partition, 1045)
+    o = BDDCOracle(pb, tau=10.0, scaling="stiffness")
+    ref = o.solve(tol=1e-8)
+    S = bddc.BDDC_SCALING_STIFFNESS
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, 10.0, scaling=S)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    assert np.isclose(st[0].omega_tilde, o.omega_tilde, rtol=1e-8)
+    assert st[0].n_coarse == o.n_coarse
+    flux32, pres32, _, _, _ = gpu_solve(bddc, [pb], 1e-8, 10.0, precision=bddc.BDDC_PREC_FP32, scaling=S)
+    assert _rel(flux32, ref.flux) <= MIXED_REL and _rel(pres32, ref.pressure) <= MIXED_REL
+    for u, p_ in ((flux, pres), (flux32, pres32)):
+        _, r2 = residuals(o.disc, u, p_)
+        assert np.abs(r2).max() <= 1e-10 * np.abs(u).max()
 
 
 @pytest.mark.parametrize("tau,seed", [(10.0, 2090), (100.0, 2090), (10.0, 2136)])

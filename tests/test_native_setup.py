@@ -246,3 +246,33 @@ def test_incompatible_pure_flux_data_solve_the_compatible_part():
     assert np.abs(r1).max() <= 1e-9 * np.abs(flux).max()
     mean_source = pb.f.sum() * pb.grid.cell_volume / pb.grid.n_cells
     assert np.allclose(np.abs(r2), abs(mean_source), rtol=1e-8)
+
+
+@pytest.mark.parametrize("case", ["c1", "irregular2d", "tiny3d"])
+@pytest.mark.parametrize("tau", [None, 4.0])
+def test_stiffness_scaling_setup_matches_oracle(case, tau):
+    """BDDC_SCALING_STIFFNESS: the native weights equal the oracle's (one
+    value per face side, Sec. 3 Remark "scaling"), and the packed setup,
+    replayed with the kernel's arithmetic, matches the oracle's stiffness-
+    scaled solve: iterations, kappa, omega-tilde and the adaptive coarse
+    space (the w-weighted face eigenproblems), and the solution at tol
+    1e-12."""
+    pb = CASES[case]()
+    opt = bddc.default_options(tau=tau or 0.0, scaling=bddc.BDDC_SCALING_STIFFNESS)
+    hs = bddc.HostSetup([pb], opt)
+    P = Packed(hs)
+    o = BDDCOracle(pb, tau=tau, scaling="stiffness")
+    off, w = hs.get("off_slot"), hs.get("slot_w")
+    for s, sub in enumerate(o.ss.subs):
+        assert np.allclose(w[off[s]:off[s + 1]], sub.weights, rtol=1e-13, atol=0)
+    _, _, its, al, be = emulate_solve(P, pb.f, pb.bc_value, 1e-8)
+    r = o.solve(tol=1e-8)
+    assert abs(int(its[0]) - r.iterations) <= iteration_slack(r.iterations, r.kappa)
+    assert abs(lanczos_condition(al[0], be[0]) - r.kappa) <= 1e-2 * r.kappa
+    flux, pres, _, _, _ = emulate_solve(P, pb.f, pb.bc_value, 1e-12)
+    r = o.solve(tol=1e-12)
+    assert np.linalg.norm(flux - r.flux) <= 1e-9 * np.linalg.norm(r.flux)
+    assert np.linalg.norm(pres - r.pressure) <= 1e-8 * np.linalg.norm(r.pressure)
+    if tau is not None:
+        assert np.isclose(hs.get("inst_omega")[0], o.omega_tilde, rtol=1e-8)
+        assert int(hs.get("inst_ncn")[0]) == o.n_coarse
