@@ -4,9 +4,13 @@ Workload (one step = one bddc_solve of a batch): the 2D 60 x 220 channelized
 field of 20 x 10 ft cells (6 x 22 subdomains of 10 x 10, log10 k from -3 to 4,
 contrast ~1e7), pressure drop along x, adaptive constraints with tau = 10,
 subdomain corrections and coarse basis in FP32 with the FP64 CG, a batch of B
-independent seeded fields solved by one persistent kernel.  Beside it the
-plain FP64 one-solve-at-a-time path is timed on the same kind of field
-(solves/s and p50/p99 latency).
+independent seeded fields solved by one persistent kernel.  Beside it, in
+the same JSON line: the same batch on the plain FP64 path, the plain FP64
+one-solve-at-a-time path on the same kind of field (solves/s and p50/p99
+latency, without and with the per-request setup), the 60 x 220 x 85
+configurations (c3: 12 x 44 x 17 boxes of 5^3; c4: seeded boxes of 3-8
+cells per axis) with their own roofline fractions, and the serving stream
+(config 5) at each arrival rate.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 a bounded sample of the same workload instead.
@@ -45,9 +49,14 @@ def parse():
     ap.add_argument("--single-solves", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-dir", default=None, help="directory for the raw nvidia-smi clock samples")
-    ap.add_argument("--serving-requests", type=int, default=200,
-                    help="requests of the serving stream (0: skip it)")
-    ap.add_argument("--serving-rate", type=float, default=200.0, help="Poisson arrival rate of the stream (1/s)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of each serving stream (0: skip serving)")
+    ap.add_argument("--serving-rates", default="50,100,200,500",
+                    help="Poisson arrival rates of the serving streams (1/s), comma-separated")
+    ap.add_argument("--large", default="c3,c4",
+                    help="60x220x85 configurations timed beside the headline (comma-separated; '' for none)")
+    ap.add_argument("--large-steps", type=int, default=5, help="timed solves of each large configuration")
+    ap.add_argument("--no-fp64-batch", action="store_true", help="skip the batched FP64 line")
     return ap.parse_args()
 
 
@@ -198,25 +207,72 @@ def measured_traffic(batch):
         return None
 
 
-def cpu_baseline(tau, tol, min_seconds=10.0, max_solves=200):
-    """The oracle as it stands on one field of the workload (setup untimed):
-    repeated solves for at least min_seconds of wall time.  cores = the
-    process's CPU time over the wall time of the sample (the threads NumPy and
-    SciPy actually kept busy)."""
-    from synth import make_config
+def _oracle_rate(pb, tau, tol, min_seconds, max_solves=200):
+    """Repeated oracle solves of one problem (setup untimed) for at least
+    min_seconds of wall time: (solves/s, cores kept busy, solves, seconds,
+    iterations)."""
     from oracle import BDDCOracle
-    pb = make_config("c2", seed=2090)
     o = BDDCOracle(pb, tau=tau)
     t0, c0 = time.perf_counter(), time.process_time()
     its = []
     while len(its) < max_solves and (not its or time.perf_counter() - t0 < min_seconds):
         its.append(o.solve(tol=tol).iterations)
     dt, cpu = time.perf_counter() - t0, time.process_time() - c0
-    n = len(its)
-    return {"value": n / dt, "unit": "solves/s", "cores": round(cpu / dt, 2), "kind": "oracle",
-            "sample": f"{n} solves of one 60x220 channelized field in {dt:.1f} s (tau={tau:g}, tol={tol:g}, "
-                      f"{its[0]} CG iterations), oracle setup excluded; NumPy/SciPy FP64 on a "
-                      f"{os.cpu_count()}-core host"}
+    return len(its) / dt, round(cpu / dt, 2), len(its), dt, its[0]
+
+
+def _one_thread_rate(tau, tol, min_seconds):
+    """The same c2 sample in a child process whose BLAS and OpenMP pools have
+    one thread (the variables must be set before NumPy loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; from synth import make_config; "
+            "r = bench._oracle_rate(make_config('c2', seed=2090), %r, %r, %r); print(json.dumps(r))"
+            % (ROOT, tau, tol, min_seconds))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, not fatal
+        return {"error": str(exc)[:200]}
+
+
+def _c3_shaped():
+    """A block of the 60x220x85 workload's shape: 20x20x15 cells of
+    20x10x2 ft, 4x4x3 subdomains of 5^3, the same 3D field generator."""
+    from synth.problems import Grid, Problem, box_partition, pressure_drop_bc, layered_3d
+    g = Grid(3, (20, 20, 15), (20.0, 10.0, 2.0))
+    t, v = pressure_drop_bc(g)
+    return Problem("c3-shaped", g, layered_3d(g, 1901), box_partition(g, (4, 4, 3)), t, v, np.zeros(g.n_cells))
+
+
+def cpu_baseline(tau, tol, min_seconds=10.0):
+    """The oracle as it stands (NumPy/SciPy FP64, setup excluded) on the
+    host cores: one c2 field with all cores and with one BLAS thread, and a
+    c3-shaped block (48 subdomains of the 60x220x85 partition's 5^3 boxes)
+    whose rate is also extrapolated to the full 8976-subdomain c3 solve by
+    subdomain-iterations.  cores = CPU time over wall time of the sample."""
+    from synth import make_config
+    v, cores, n, dt, it0 = _oracle_rate(make_config("c2", seed=2090), tau, tol, min_seconds)
+    one = _one_thread_rate(tau, tol, min_seconds)
+    v3, cores3, n3, dt3, it3 = _oracle_rate(_c3_shaped(), tau, tol, min_seconds / 2)
+    c3_its, c3_subs = 42, 8976
+    out = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n} solves of one 60x220 channelized field in {dt:.1f} s (tau={tau:g}, tol={tol:g}, "
+                     f"{it0} CG iterations), oracle setup excluded; NumPy/SciPy FP64 on a "
+                     f"{os.cpu_count()}-core host"}
+    if isinstance(one, list):
+        out["one_thread"] = {"value": one[0], "unit": "solves/s", "cores": one[1],
+                             "sample": f"{one[2]} solves of the same field with one BLAS/OpenMP thread"}
+    else:
+        out["one_thread"] = one
+    out["c3_shaped"] = {"value": v3, "unit": "solves/s", "cores": cores3, "iterations": it3,
+                        "sample": f"{n3} solves of a 20x20x15 block of the 60x220x85 workload (4x4x3 "
+                                  f"subdomains of 5^3, tau={tau:g}) in {dt3:.1f} s",
+                        "c3_seconds_per_solve_extrapolated": (1.0 / v3) * (c3_subs / 48.0) * (c3_its / max(1, it3)),
+                        "extrapolation": "per subdomain-iteration time of the block times 8976 subdomains x "
+                                         "42 iterations of the full c3 solve (the oracle's coarse solve grows "
+                                         "faster than linearly: a lower bound)"}
+    return out
 
 
 def run_reference(args):
@@ -251,21 +307,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def serving_run(args, rank):
-    """The serving stream: independent 2D channelized fields of 30-60 x
-    110-220 cells (10 x 10-cell subdomains, random pressure-drop direction)
-    arriving as a seeded Poisson process, submitted to the library's serving
-    loop (continuous batching, admission by HBM footprint).  Reports solves/s
-    over the stream and the p50/p99 of submission-to-result latency, which
-    includes each request's own setup."""
+def serving_run(args, rank, rate):
+    """The serving stream (config 5): independent 2D channelized fields of
+    30-60 x 110-220 cells (10 x 10-cell subdomains, random pressure-drop
+    direction) arriving as a seeded Poisson process at `rate` per second,
+    submitted to the library's serving loop (continuous batching, admission
+    by HBM footprint).  Reports solves/s over the stream and the p50/p99 of
+    submission-to-result latency, which includes each request's own setup."""
     from paper_1901_02090_gb300 import bddc
     from synth.problems import serving_request
-    n, rate = args.serving_requests, args.serving_rate
+    n = args.serving_requests
     pbs = [serving_request(rank * 1000003 + i) for i in range(n)]
-    gaps = np.random.default_rng(7 + rank).exponential(1.0 / rate, size=n)
+    gaps = np.random.default_rng(7 + rank + int(rate)).exponential(1.0 / rate, size=n)
     srv = bddc.Server(bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32),
                       hbm_budget_bytes=16 << 30, max_batch=64)
-    pending, lat, its, batches = [], [], [], set()
+    pending, lat, its, batches, setup_ms, queue_ms = [], [], [], set(), [], []
     t0 = time.perf_counter()
     t_next = t0
     for i, pb in enumerate(pbs):
@@ -279,6 +335,8 @@ def serving_run(args, rank):
         rc, _, _, it, _, info = srv.poll(t)
         failed += rc != bddc.BDDC_OK
         lat.append(info.latency_ms)
+        setup_ms.append(info.setup_ms)
+        queue_ms.append(info.queue_ms)
         its.append(it)
         batches.add(info.batch_id)
     wall = time.perf_counter() - t0
@@ -286,11 +344,116 @@ def serving_run(args, rank):
     srv.close()
     lat = np.array(lat)
     return {"value": n / wall, "unit": "solves/s", "requests": n, "arrival_rate_per_s": rate,
+            "offered_span_s": float(np.sum(gaps)), "wall_s": wall,
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "mean_setup_ms": float(np.mean(setup_ms)), "mean_queue_ms": float(np.mean(queue_ms)),
             "failed": int(failed), "batches": len(batches), "mean_batch": n / max(1, len(batches)),
-            "iterations_mean": float(np.mean(its)), "device_bytes_peak": int(peak),
-            "workload": "30-60 x 110-220 channelized fields, 10x10-cell subdomains, random pressure direction, "
-                        "tau=%g, mixed path; latency includes each request's host setup" % args.tau}
+            "iterations_mean": float(np.mean(its)), "device_bytes_peak": int(peak)}
+
+
+def large_config(args, name, dev, stream, peak):
+    """One 60x220x85 field (c3: 12x44x17 boxes of 5^3; c4: seeded boxes of
+    3-8 cells per axis), tau = 10, mixed path, the sparse coarse solver
+    (chosen automatically): device time per solve over `large_steps` solves,
+    iterations, algorithmic bytes per launch and their fraction of the
+    measured copy bandwidth, setup time and the true residual."""
+    import torch
+    from paper_1901_02090_gb300 import bddc
+    from synth import make_config
+    pb = make_config(name)
+    t0 = time.perf_counter()
+    h = bddc.setup([pb], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32),
+                   stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    f = torch.as_tensor(pb.f, device=dev)
+    bc = torch.as_tensor(pb.bc_value, device=dev)
+    flux = torch.empty(len(pb.bc_value), dtype=torch.float64, device=dev)
+    pres = torch.empty(pb.grid.n_cells, dtype=torch.float64, device=dev)
+    h.solve(f, bc, args.tol, flux, pres)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kb = [], []
+    ev0.record(stream)
+    for _ in range(max(1, args.large_steps)):
+        h.solve(f, bc, args.tol, flux, pres)
+        ms, by = h.last_solve_timing()
+        kms.append(ms)
+        kb.append(by)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    st = h.stats(0)
+    wall = ev0.elapsed_time(ev1) / len(kms)
+    h.close()
+    km, by = float(np.mean(kms)), float(np.mean(kb))
+    ach = by / (km / 1e3) / 1e9
+    return {"workload": f"{name}: 60x220x85 cells (20x10x2 ft), " +
+                        ("12x44x17 subdomains of 5^3" if name == "c3" else "seeded boxes of 3-8 cells per axis") +
+                        f", tau={args.tau:g}, mixed path, sparse coarse solver",
+            "ms_per_solve": wall, "kernel_ms": km, "solves_per_s": 1e3 / wall,
+            "iterations": st.iterations, "n_subdomains": st.n_subdomains, "n_coarse": st.n_coarse,
+            "true_relres": st.true_relres, "setup_s": round(setup_s, 2),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes_per_launch": by}}
+
+
+def batched_fp64(args, pbs, dev, stream, peak, K):
+    """The same batch on the plain FP64 path (every operator FP64): device
+    time per batch over K solves; separates the precision gain from the
+    batching gain."""
+    import torch
+    from paper_1901_02090_gb300 import bddc
+    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64), stream=stream.cuda_stream)
+    f = torch.as_tensor(np.concatenate([pb.f for pb in pbs]), device=dev)
+    bc = torch.as_tensor(np.concatenate([pb.bc_value for pb in pbs]), device=dev)
+    flux = torch.empty(len(bc), dtype=torch.float64, device=dev)
+    pres = torch.empty(len(f), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        h.solve(f, bc, args.tol, flux, pres)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kb = [], []
+    ev0.record(stream)
+    for _ in range(K):
+        h.solve(f, bc, args.tol, flux, pres)
+        ms, by = h.last_solve_timing()
+        kms.append(ms)
+        kb.append(by)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total = ev0.elapsed_time(ev1)
+    its = [h.stats(i).iterations for i in range(len(pbs))]
+    tr = max(h.stats(i).true_relres for i in range(len(pbs)))
+    h.close()
+    km, by = float(np.mean(kms)), float(np.mean(kb))
+    ach = by / (km / 1e3) / 1e9
+    return {"value": len(pbs) * K / (total / 1e3), "unit": "solves/s", "batch": len(pbs), "steps": K,
+            "ms_per_step": total / K, "kernel_ms": km, "iterations_mean": float(np.mean(its)),
+            "true_relres_max": tr,
+            "roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "algorithmic_bytes_per_launch": by}}
+
+
+def single_with_setup(args, pb1, stream, n=10):
+    """The plain FP64 path one request at a time with its own setup (what a
+    request costs without batching): bddc_setup + bddc_solve + the result
+    copies per request, host buffers."""
+    from paper_1901_02090_gb300 import bddc
+    flux = np.empty(len(pb1.bc_value))
+    pres = np.empty(pb1.grid.n_cells)
+    opt = bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64)
+    h = bddc.setup([pb1], opt, stream=stream.cuda_stream)
+    h.solve(pb1.f, pb1.bc_value, args.tol, flux, pres)
+    h.close()
+    lat = []
+    for _ in range(n):
+        t0 = time.perf_counter()
+        h = bddc.setup([pb1], opt, stream=stream.cuda_stream)
+        h.solve(pb1.f, pb1.bc_value, args.tol, flux, pres)
+        h.close()
+        lat.append((time.perf_counter() - t0) * 1e3)
+    return {"value": 1e3 / float(np.mean(lat)), "unit": "solves/s", "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "requests": n,
+            "note": "setup (host + GPU local maps and face eigenproblems + upload) and solve per request, FP64"}
 
 
 def single_path(args, pb1, dev, stream, formulation=0):
@@ -401,19 +564,35 @@ def main():
     e2e_value = whole_job_value(world, B, K, e2e_ms)
     h.close()
 
+    peak, peak_kind = measured_peak()
+
+    # ---- the same batch on the plain FP64 path ------------------------------------
+    fp64_batch = None if args.no_fp64_batch else batched_fp64(args, pbs, dev, stream, peak, max(3, K // 3))
+
     # ---- plain FP64 one-solve-at-a-time path ------------------------------------
-    fp64_single = full_single = None
+    fp64_single = full_single = single_setup = None
     if args.single_solves > 0:
         fp64_single = single_path(args, pbs[0], dev, stream)
         full_single = single_path(args, pbs[0], dev, stream, bddc.BDDC_FORM_FULL)
         full_single["note"] = ("the same FP64 solve with the Step-3 operator in its full-space form: the RT0/P0 "
                                "operator applied matrix-free to the discrete-harmonic extension of each direction")
+        single_setup = single_with_setup(args, pbs[0], stream)
 
-    serving = serving_run(args, rank) if args.serving_requests > 0 else None
+    # ---- the 60x220x85 configurations ---------------------------------------------
+    large = {}
+    for name in [x for x in args.large.split(",") if x]:
+        large[name] = large_config(args, name, dev, stream, peak)
+
+    serving = None
+    if args.serving_requests > 0:
+        rates = [float(x) for x in args.serving_rates.split(",") if x]
+        serving = {"workload": "config 5: 30-60 x 110-220 channelized fields, 10x10-cell subdomains, random "
+                               "pressure direction, tau=%g, mixed path; latency includes each request's setup"
+                               % args.tau,
+                   "rates": [serving_run(args, rank, r) for r in rates]}
 
     if rank != 0:
         return
-    peak, peak_kind = measured_peak()
     avg_ms = float(np.mean(kms))
     avg_bytes = float(np.mean(kbytes))
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
@@ -429,8 +608,11 @@ def main():
         "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
         # ||r|| / ||rhs|| of the full RT0/P0 system at each returned solution (GPU, after the solve)
         "true_relres_max": float(np.max(true_res)),
+        "fp64_batch": fp64_batch,
         "fp64_single": fp64_single,
+        "fp64_single_with_setup": single_setup,
         "full_form_single": full_single,
+        **large,
         "serving": serving,
         "latency_batched_ms": {"p50": float(np.percentile(kms, 50)), "p99": float(np.percentile(kms, 99)),
                                "per_step_wall": total_ms / K, "note": "kernel time of one batch (CUDA events)"},

@@ -148,6 +148,7 @@ __device__ void cg_decide(const Params& p, int b, int k, double rz, bool fp64_co
             p.st[b].status = status;
             p.st[b].iterations = k;
             p.st[b].relres = relres;
+            p.st[b].fin = phase_index(k, kPhProlong) + 1;
             __threadfence();
             p.st[b].done = 1;
             atomicSub(p.n_active, 1);
@@ -164,6 +165,7 @@ __device__ void cg_alpha(const Params& p, int b, int k, double dq) {
         p.st[b].status = BDDC_E_BREAKDOWN;
         p.st[b].iterations = k;
         p.st[b].relres = -1.0;
+        p.st[b].fin = phase_index(k, kPhDirop) + 1;
         __threadfence();
         p.st[b].done = 1;
         atomicSub(p.n_active, 1);
@@ -312,6 +314,10 @@ struct WarpSm {
 struct CtaSm {
     double* rhs;  // staged coarse right-hand side (CTA-level)
     WarpSm w;
+    // active-instance snapshot of the current CG iteration (p.act_n > 0):
+    // exclusive prefix sums over the instances of the active subdomains
+    // (act_sub) and of the active coarse units (act_cu), n_inst + 1 each
+    int *act_sub, *act_cu;
 };
 // kExt: the warp areas include the full form's extension (max_ext doubles)
 template <bool kExt = false>
@@ -327,7 +333,84 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     c.w.xin = wb + 2 * p.max_ng;
     c.w.wcs = c.w.xin + p.max_in_post;
     c.w.tsum = c.w.wcs + p.max_m + 1;
+    c.act_sub = reinterpret_cast<int*>(base + p.max_ncn + (int64_t)kWarps * per_warp);
+    c.act_cu = c.act_sub + p.act_n + 1;
     return c;
+}
+
+// Snapshot of the instances active in CG phase P (fin = 0 or fin > P), per
+// CTA: exclusive prefix sums over the instances of their subdomain counts
+// and coarse-unit counts (0 for inactive instances).  Whole CTA; returns
+// the number of active subdomains.  Every CTA computes the same snapshot.
+__device__ int64_t active_snapshot(const Params& p, const CtaSm& sm, int P) {
+    const int n = p.act_n;
+    const int per = (n + kThreads - 1) / kThreads;
+    const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    // fin is read once: bit t of `on` is instance i0 + t (per <= 16 for kActMaxInst)
+    int cs = 0, cu = 0;
+    unsigned on = 0u;
+    for (int b = i0; b < i1; ++b) {
+        const int f = __ldcg(&p.st[b].fin);
+        if (f == 0 || f > P) {
+            on |= 1u << (b - i0);
+            cs += (int)(p.inst_s1[b] - p.inst_s0[b]);
+            cu += (int)(p.inst_cu0[b + 1] - p.inst_cu0[b]);
+        }
+    }
+    // block exclusive scan of (cs, cu): warp scans, then the warp totals
+    __shared__ int wtot[2 * kWarps];
+    const int l = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    int xs = cs, xu = cu;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ys = __shfl_up_sync(0xffffffffu, xs, o), yu = __shfl_up_sync(0xffffffffu, xu, o);
+        if (l >= o) {
+            xs += ys;
+            xu += yu;
+        }
+    }
+    __syncthreads();
+    if (l == 31) {
+        wtot[wi] = xs;
+        wtot[kWarps + wi] = xu;
+    }
+    __syncthreads();
+    int bs = 0, bu = 0;
+    for (int q = 0; q < wi; ++q) {
+        bs += wtot[q];
+        bu += wtot[kWarps + q];
+    }
+    int es = bs + xs - cs, eu = bu + xu - cu;  // exclusive prefix of this thread's first instance
+    for (int b = i0; b < i1; ++b) {
+        sm.act_sub[b] = es;
+        sm.act_cu[b] = eu;
+        if (on & (1u << (b - i0))) {
+            es += (int)(p.inst_s1[b] - p.inst_s0[b]);
+            eu += (int)(p.inst_cu0[b + 1] - p.inst_cu0[b]);
+        }
+    }
+    if (threadIdx.x == kThreads - 1) {
+        int ts = 0, tu = 0;
+        for (int q = 0; q < kWarps; ++q) {
+            ts += wtot[q];
+            tu += wtot[kWarps + q];
+        }
+        sm.act_sub[n] = ts;
+        sm.act_cu[n] = tu;
+    }
+    __syncthreads();
+    return sm.act_sub[n];
+}
+
+// the instance b with pre[b] <= x < pre[b + 1] (pre non-decreasing, n + 1 entries)
+__device__ __forceinline__ int act_find(const int* pre, int n, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // stage x[0..n) as FP32 (hi only: inputs of the FP32 operators)
@@ -1081,12 +1164,26 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         p.tstamp[1] = t;
         nts = 1;
     }
+    // set per CG iteration: some instances have left the loop, and the CG
+    // phases spread the active instances' work over all warps and CTAs
+    bool partial = false;
     auto coarse_phase = [&](bool step1) {
         staged = -1;
-        cta_range(p.n_cunits, a, e);
-        for (int64_t u = a; u < e; ++u) {
+        auto unit = [&](int64_t u) {
             if constexpr (MX) mx_coarse(p, u, step1, sm.rhs, staged);
             else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
+        };
+        if (partial && !step1) {
+            // the active instances' coarse units, split evenly over the CTAs
+            cta_range(sm.act_cu[p.act_n], a, e);
+            int b = -1;
+            for (int64_t x = a; x < e; ++x) {
+                if (b < 0 || x >= sm.act_cu[b + 1]) b = act_find(sm.act_cu, p.act_n, x);
+                unit(p.inst_cu0[b] + (x - sm.act_cu[b]));
+            }
+        } else {
+            cta_range(p.n_cunits, a, e);
+            for (int64_t u = a; u < e; ++u) unit(u);
         }
     };
     // a coarse solve and the grid barrier(s) after it: the dense inverse in
@@ -1144,16 +1241,30 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     // a CG phase over the warp's subdomains; the arrivals of its consecutive
     // subdomains of one instance are counted at once (publish_total)
     auto cg_phase = [&](int ctr, int kk, auto&& unit) {
-        sub_range(p, a, e);
         int cur = -1, n = 0;
-        for (int64_t s = a; s < e; ++s) {
-            const int b = p.sub_inst[s];
+        auto visit = [&](int64_t s, int b) {
             if (b != cur) {
                 if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
                 cur = b;
                 n = 0;
             }
             if (unit(s)) ++n;
+        };
+        if (partial) {
+            // the active instances' subdomains in instance order, split
+            // evenly over the warps (by count: the subdomains of a batch are
+            // alike; a single instance keeps the work-balanced ranges)
+            const int64_t W = (int64_t)gridDim.x * kWarps;
+            const int64_t wg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+            const int64_t A = sm.act_sub[p.act_n];
+            int b = -1;
+            for (int64_t x = (A * wg) / W; x < (A * (wg + 1)) / W; ++x) {
+                if (b < 0 || x >= sm.act_sub[b + 1]) b = act_find(sm.act_sub, p.act_n, x);
+                visit(p.inst_s0[b] + (x - sm.act_sub[b]), b);
+            }
+        } else {
+            sub_range(p, a, e);
+            for (int64_t s = a; s < e; ++s) visit(s, p.sub_inst[s]);
         }
         if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
     };
@@ -1165,7 +1276,17 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     cg_phase(kCtrRZ, 0, prolong_unit);
     if (!phase_end(p, 7, nts)) return;
     for (int k = 0;; ++k) {
-        if (__ldcg(p.n_active) <= 0) break;
+        // the instances still in the loop: every CTA takes the same snapshot
+        // (phase_index), so all leave the loop at the same iteration; with
+        // more than kActMaxInst instances the count of active instances is
+        // read instead (the snapshot is off)
+        if (p.act_n > 0) {
+            const int64_t nact = active_snapshot(p, sm, phase_index(k, kPhDirop));
+            if (nact == 0) break;
+            partial = nact < p.n_sub;
+        } else if (__ldcg(p.n_active) <= 0) {
+            break;
+        }
         cg_phase(kCtrDQ, k, [&](int64_t s) -> bool {
             if constexpr (MX) return mx_dirop(p, s, k, w);
             else if constexpr (PR::kFull) return ph_dirop_full<PR>(p, s, k, w);
@@ -1181,6 +1302,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         cg_phase(kCtrRZ, k + 1, prolong_unit);
         if (!phase_end(p, 7, nts)) return;
     }
+    partial = false;
     if constexpr (MX) {
         // closing FP64 coarse pressure correction (every instance is done;
         // the coarse phase runs in step-1 layout with a zero pressure part)
@@ -1657,11 +1779,14 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     }
     // coarse work units
     std::vector<int> cu_inst, cu_row0;
-    for (int b = 0; b < n_instances; ++b)
+    std::vector<int64_t> cu0(1, 0);
+    for (int b = 0; b < n_instances; ++b) {
         for (int64_t r0 = 0; r0 < P.inst_ncn[b]; r0 += kCoarseRows) {
             cu_inst.push_back(b);
             cu_row0.push_back((int)r0);
         }
+        cu0.push_back((int64_t)cu_inst.size());
+    }
     h->inst_cfoff.assign(n_instances, 0);
     for (int b = 1; b < n_instances; ++b) h->inst_cfoff[b] = h->inst_cfoff[b - 1] + P.inst_ncf[b - 1];
     Params& p = h->prm;
@@ -1678,7 +1803,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     UP(sub_d, P.sub_d); UP(slot_g, P.slot_g); UP(slot_partner, P.slot_partner); UP(slot_w, P.slot_w);
     UP(slot_dsig, P.slot_dsig); UP(cslot_c, P.cslot_c); UP(cell_gid, P.cell_gid); UP(int_fid, P.int_fid);
     UP(g_fid, P.g_fid); UP(g_bsign, P.g_bsign); UP(c_slot_a, P.c_slot_a); UP(c_slot_b, P.c_slot_b);
-    UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0);
+    UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0); UP(inst_cu0, cu0);
     if (opt.formulation == BDDC_FORM_FULL) {
         UP(slot_fk, P.slot_fk); UP(slot_fopp, P.slot_fopp); UP(slot_fcell, P.slot_fcell);
     }
@@ -1851,8 +1976,10 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     p.max_ncn = P.coarse_sparse ? 2 : std::max(P.max_ncn, 1);  // the CTA rhs area of the dense coarse solve
     p.max_m = std::max(P.max_m, 1);
     p.max_ext = opt.formulation == BDDC_FORM_FULL ? std::max(P.max_out_post, 1) : 0;
+    p.act_n = n_instances <= kActMaxInst ? n_instances : 0;
     h->smem = sizeof(double) * ((size_t)p.max_ncn + (size_t)kWarps * (2 * (size_t)p.max_ng + p.max_in_post +
-                                                                       2 * ((size_t)p.max_m + 1) + p.max_ext));
+                                                                       2 * ((size_t)p.max_m + 1) + p.max_ext)) +
+              sizeof(int) * 2 * ((size_t)p.act_n + 1);
     if (h->smem > 200 * 1024) {
         bddc_destroy(h);
         return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve

@@ -31,6 +31,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCoarseRows = 16;             // coarse rows per work unit
 constexpr long long kBarrierWaitNs = 10000000000LL;  // a grid-barrier wait past 10 s is an error
+constexpr int kActMaxInst = 4096;           // largest batch whose CG phases are rebalanced over active instances
 
 struct GridSync {
     unsigned int count;
@@ -44,9 +45,18 @@ struct InstState {
     int done;        // 1 once the instance left the CG loop
     int status;      // BDDC_OK / BDDC_E_NOT_CONVERGED / BDDC_E_BREAKDOWN
     int iterations;
-    int pad;
+    int fin;         // 1 + the CG phase (phase_index) in which it left the loop; 0 while active
     double r0, floor, rho0, relres;
 };
+
+// Index of a CG phase, for the active-instance snapshots: the PROLONG that
+// decides iteration k (its convergence test) is 4k, the DIROP, UPDATE and
+// COARSE of iteration k are 4k + 1, 4k + 2, 4k + 3.  An instance whose fin
+// is 0 or above P is active in phase P: a warp reading fin during the phase
+// in which it is written sees either 0 or P + 1, both "active", so all warps
+// of a phase agree.
+__host__ __device__ constexpr int phase_index(int k, int kind) { return 4 * k + kind; }
+enum : int { kPhProlong = 0, kPhDirop = 1, kPhUpdate = 2, kPhCoarse = 3 };
 
 struct Params {
     // instances
@@ -78,9 +88,13 @@ struct Params {
     // axis and the cell with the face's side (see the setup's Packed)
     const double* slot_fk;
     const int *slot_fopp, *slot_fcell;
-    // coarse units
+    // coarse units (inst_cu0: first unit of each instance, n_inst + 1 entries)
     int64_t n_cunits;
     const int *cunit_inst, *cunit_row0;
+    const int64_t* inst_cu0;
+    // active-instance snapshots (per CTA, in shared memory): 0 = off (one
+    // instance, or more than kActMaxInst), else n_inst
+    int act_n;
     // matrices: S and Kinv are double (FP64 path) or float2 pairs (mixed);
     // F and P are double or float; P64 is always FP64
     const void *S, *F, *P, *Kinv;

@@ -166,6 +166,44 @@ def _flux_equation_residual_sample(disc, flux, pres, n_sample, seed):
     return np.array(res), np.array(scale)
 
 
+@pytest.fixture(scope="module")
+def mid3d():
+    """40 x 40 x 20 cells of the 60x220x85 workload's field generator and
+    cell size, 8 x 8 x 4 subdomains of 5^3 (256: the dissection tree has 32
+    leaves and 6 levels), tau = 10; the oracle solve at tol 1e-8 (about 90 s
+    of oracle setup)."""
+    pb = _box3d(40, 40, 20, seed=1902)
+    o = BDDCOracle(pb, tau=10.0)
+    return pb, o, o.solve(tol=1e-8)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mid_size_3d_sparse_coarse_matches_oracle(bddc, mid3d, precision):
+    """A mid-size 3D case between the 48-subdomain parity cases and the
+    full-size 60x220x85 runs, with the sparse coarse solver forced: the
+    sweeps run over a tree of 6 levels (checked in the packed setup), and
+    the result matches the oracle (FP64 within 1e-8 x kappa and iterations
+    within the slack, mixed within 1e-6), cellwise conservative."""
+    pb, o, ref = mid3d
+    hs = bddc.HostSetup([pb], bddc.default_options(tau=10.0, coarse_solver=bddc.BDDC_COARSE_SPARSE))
+    assert int(hs.get("cn_depth").max()) + 1 >= 6
+    hs.close()
+    rc, flux, pres, its, st = _solve(bddc, pb, 1e-8, 10.0, precision, bddc.BDDC_COARSE_SPARSE)
+    assert rc == bddc.BDDC_OK and st.n_subdomains == 256
+    assert st.n_coarse == o.n_coarse
+    assert np.isclose(st.omega_tilde, o.omega_tilde, rtol=1e-8)
+    if precision == 0:
+        assert abs(its - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+        assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+        assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    else:
+        assert _rel(flux, ref.flux) <= MIXED_REL and _rel(pres, ref.pressure) <= MIXED_REL
+    disc = o.disc
+    cf = disc.cell_faces
+    div = sum(flux[cf[:, a, 0]] - flux[cf[:, a, 1]] for a in range(3))
+    assert np.abs(disc.cell_rhs() - div).max() <= 1e-10 * np.abs(flux).max()
+
+
 @pytest.mark.parametrize("name,n_sub", [("c3", 8976), ("c4", 7568)])
 def test_3d_full_size_converges_conservative(bddc, name, n_sub):
     """60x220x85 cells (1.12M cells, 3.4M faces), 12x44x17 subdomains of 5^3
@@ -189,7 +227,10 @@ def test_3d_full_size_converges_conservative(bddc, name, n_sub):
     assert rc == bddc.BDDC_OK and st.status == bddc.BDDC_OK
     assert st.n_subdomains == n_sub and st.n_coarse > bddc.BDDC_COARSE_DENSE_MAX
     assert st.relres <= 1e-8
-    assert st.true_relres <= 1e-6  # the full saddle system at the returned solution (GPU, matrix-free)
+    # the full saddle system at the returned solution (GPU, matrix-free): a
+    # reduced residual of 1e-8 leaves the full one at or below that (4e-10
+    # on c3, 6e-11 on c4)
+    assert st.true_relres <= 1e-8
     assert np.all(np.isfinite(flux)) and np.all(np.isfinite(pres))
     disc = Discretization(pb)
     cf = disc.cell_faces
@@ -197,4 +238,8 @@ def test_3d_full_size_converges_conservative(bddc, name, n_sub):
     r2 = disc.cell_rhs() - div
     assert np.abs(r2).max() <= 1e-9 * np.abs(flux).max()
     r1, scale = _flux_equation_residual_sample(disc, flux, pres, 4000, 85)
-    assert np.max(np.abs(r1) / scale) <= 1e-5
+    worst = float(np.max(np.abs(r1) / scale))
+    print(f"{name}: largest sampled flux-equation residual / term size {worst:.2e}")
+    # the converged reduced residual (1e-8 relative) bounds the interface
+    # rows; interior rows are at the local maps' rounding level
+    assert worst <= 1e-7
