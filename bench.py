@@ -622,7 +622,7 @@ def main():
         "gpu_launches": 3 * K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(B), "peak_kind": peak_kind,
-                     "kernel": "bddc_solve_kernel<PrecMixed> (persistent Steps 1-3 + post)",
+                     "kernel": "bddc_solve_kernel<PrecMixed, true> (persistent Steps 1-3 + post, rebalanced over active instances)",
                      "kernel_ms_mean": avg_ms, "algorithmic_bytes_per_launch": avg_bytes},
         "clocks": clk,
     }

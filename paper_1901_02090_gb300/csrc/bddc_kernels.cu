@@ -314,10 +314,6 @@ struct WarpSm {
 struct CtaSm {
     double* rhs;  // staged coarse right-hand side (CTA-level)
     WarpSm w;
-    // active-instance snapshot of the current CG iteration (p.act_n > 0):
-    // exclusive prefix sums over the instances of the active subdomains
-    // (act_sub) and of the active coarse units (act_cu), n_inst + 1 each
-    int *act_sub, *act_cu;
 };
 // kExt: the warp areas include the full form's extension (max_ext doubles)
 template <bool kExt = false>
@@ -333,16 +329,29 @@ __device__ __forceinline__ CtaSm carve(const Params& p, double* base) {
     c.w.xin = wb + 2 * p.max_ng;
     c.w.wcs = c.w.xin + p.max_in_post;
     c.w.tsum = c.w.wcs + p.max_m + 1;
-    c.act_sub = reinterpret_cast<int*>(base + p.max_ncn + (int64_t)kWarps * per_warp);
-    c.act_cu = c.act_sub + p.act_n + 1;
     return c;
 }
+
+// Active-instance snapshot of the current CG iteration (p.act_n > 0), after
+// the warp areas of the persistent kernel's shared memory: exclusive prefix
+// sums over the instances of the active subdomains (act_sub) and of the
+// active coarse units (act_cu = act_sub + n_inst + 1), n_inst + 1 each.  The
+// address is formed where it is used, so that no register holds it across
+// the phases (the kernel runs at its register cap).
+template <bool kExt>
+__device__ __forceinline__ int* act_area(const Params& p, double* base) {
+    const int per_warp = 2 * p.max_ng + p.max_in_post + 2 * (p.max_m + 1) + (kExt ? p.max_ext : 0);
+    return reinterpret_cast<int*>(base + p.max_ncn + (int64_t)kWarps * per_warp);
+}
+// set by active_snapshot: the current CG iteration rebalances its phases
+__shared__ int g_partial_sh;
 
 // Snapshot of the instances active in CG phase P (fin = 0 or fin > P), per
 // CTA: exclusive prefix sums over the instances of their subdomain counts
 // and coarse-unit counts (0 for inactive instances).  Whole CTA; returns
 // the number of active subdomains.  Every CTA computes the same snapshot.
-__device__ int64_t active_snapshot(const Params& p, const CtaSm& sm, int P) {
+__device__ int64_t active_snapshot(const Params& p, int* act_sub, int P) {
+    int* act_cu = act_sub + p.act_n + 1;
     const int n = p.act_n;
     const int per = (n + kThreads - 1) / kThreads;
     const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
@@ -382,8 +391,8 @@ __device__ int64_t active_snapshot(const Params& p, const CtaSm& sm, int P) {
     }
     int es = bs + xs - cs, eu = bu + xu - cu;  // exclusive prefix of this thread's first instance
     for (int b = i0; b < i1; ++b) {
-        sm.act_sub[b] = es;
-        sm.act_cu[b] = eu;
+        act_sub[b] = es;
+        act_cu[b] = eu;
         if (on & (1u << (b - i0))) {
             es += (int)(p.inst_s1[b] - p.inst_s0[b]);
             eu += (int)(p.inst_cu0[b + 1] - p.inst_cu0[b]);
@@ -395,11 +404,12 @@ __device__ int64_t active_snapshot(const Params& p, const CtaSm& sm, int P) {
             ts += wtot[q];
             tu += wtot[kWarps + q];
         }
-        sm.act_sub[n] = ts;
-        sm.act_cu[n] = tu;
+        act_sub[n] = ts;
+        act_cu[n] = tu;
+        g_partial_sh = ts > 0 && ts < p.n_sub;
     }
     __syncthreads();
-    return sm.act_sub[n];
+    return act_sub[n];
 }
 
 // the instance b with pre[b] <= x < pre[b + 1] (pre non-decreasing, n + 1 entries)
@@ -1148,7 +1158,12 @@ __device__ void cs_backward(const Params& p, int4 un) {
 }
 
 // ---- the persistent solve kernel -------------------------------------------------------
-template <class PR>
+// kBal: the CG phases of a batch are rebalanced over the instances still
+// active (g_partial_sh, active_snapshot); without it (one instance, or more
+// than kActMaxInst) every phase keeps its work-balanced static ranges.  Two
+// instantiations, because the kernel runs at its register cap and the
+// rebalancing's bookkeeping changes the register allocation of the phases.
+template <class PR, bool kBal>
 __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     constexpr bool MX = PR::kMixed;
     extern __shared__ double smem_base[];
@@ -1164,26 +1179,30 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         p.tstamp[1] = t;
         nts = 1;
     }
-    // set per CG iteration: some instances have left the loop, and the CG
-    // phases spread the active instances' work over all warps and CTAs
-    bool partial = false;
+    // g_partial_sh (per CG iteration): some instances have left the loop,
+    // and the CG phases spread the active instances' work over all warps
+    // and CTAs
+    if (threadIdx.x == 0) g_partial_sh = 0;
     auto coarse_phase = [&](bool step1) {
         staged = -1;
-        auto unit = [&](int64_t u) {
-            if constexpr (MX) mx_coarse(p, u, step1, sm.rhs, staged);
-            else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
-        };
-        if (partial && !step1) {
-            // the active instances' coarse units, split evenly over the CTAs
-            cta_range(sm.act_cu[p.act_n], a, e);
-            int b = -1;
-            for (int64_t x = a; x < e; ++x) {
-                if (b < 0 || x >= sm.act_cu[b + 1]) b = act_find(sm.act_cu, p.act_n, x);
-                unit(p.inst_cu0[b] + (x - sm.act_cu[b]));
-            }
+        // with g_partial_sh the active instances' coarse units are split
+        // evenly over the CTAs (unit position x -> the x-th active unit)
+        const bool part = kBal && !step1 && g_partial_sh;
+        if (part) {
+            const int* act_cu = act_area<PR::kFull>(p, smem_base) + p.act_n + 1;
+            cta_range(act_cu[p.act_n], a, e);
         } else {
             cta_range(p.n_cunits, a, e);
-            for (int64_t u = a; u < e; ++u) unit(u);
+        }
+        for (int64_t x = a; x < e; ++x) {
+            int64_t u = x;
+            if (part) {
+                const int* act_cu = act_area<PR::kFull>(p, smem_base) + p.act_n + 1;
+                const int b = act_find(act_cu, p.act_n, x);
+                u = p.inst_cu0[b] + (x - act_cu[b]);
+            }
+            if constexpr (MX) mx_coarse(p, u, step1, sm.rhs, staged);
+            else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
         }
     };
     // a coarse solve and the grid barrier(s) after it: the dense inverse in
@@ -1241,30 +1260,36 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     // a CG phase over the warp's subdomains; the arrivals of its consecutive
     // subdomains of one instance are counted at once (publish_total)
     auto cg_phase = [&](int ctr, int kk, auto&& unit) {
+        // positions [a, e) of this warp: its work-balanced subdomain range,
+        // or with g_partial_sh an even share of the active instances'
+        // subdomains in instance order (by count: the subdomains of a batch
+        // are alike), position x -> the x-th active subdomain
+        if (kBal && g_partial_sh) {
+            const int64_t A = act_area<PR::kFull>(p, smem_base)[p.act_n];
+            const int64_t W = (int64_t)gridDim.x * kWarps;
+            const int64_t wg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+            a = (A * wg) / W;
+            e = (A * (wg + 1)) / W;
+        } else {
+            sub_range(p, a, e);
+        }
         int cur = -1, n = 0;
-        auto visit = [&](int64_t s, int b) {
+        for (int64_t x = a; x < e; ++x) {
+            int64_t s = x;
+            int b;
+            if (kBal && g_partial_sh) {
+                const int* act_sub = act_area<PR::kFull>(p, smem_base);
+                b = act_find(act_sub, p.act_n, x);
+                s = p.inst_s0[b] + (x - act_sub[b]);
+            } else {
+                b = p.sub_inst[s];
+            }
             if (b != cur) {
                 if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
                 cur = b;
                 n = 0;
             }
             if (unit(s)) ++n;
-        };
-        if (partial) {
-            // the active instances' subdomains in instance order, split
-            // evenly over the warps (by count: the subdomains of a batch are
-            // alike; a single instance keeps the work-balanced ranges)
-            const int64_t W = (int64_t)gridDim.x * kWarps;
-            const int64_t wg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-            const int64_t A = sm.act_sub[p.act_n];
-            int b = -1;
-            for (int64_t x = (A * wg) / W; x < (A * (wg + 1)) / W; ++x) {
-                if (b < 0 || x >= sm.act_sub[b + 1]) b = act_find(sm.act_sub, p.act_n, x);
-                visit(p.inst_s0[b] + (x - sm.act_sub[b]), b);
-            }
-        } else {
-            sub_range(p, a, e);
-            for (int64_t s = a; s < e; ++s) visit(s, p.sub_inst[s]);
         }
         if (n > 0) publish_total(p, cur, n, ctr, kk, false, !MX);
     };
@@ -1281,9 +1306,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         // more than kActMaxInst instances the count of active instances is
         // read instead (the snapshot is off)
         if (p.act_n > 0) {
-            const int64_t nact = active_snapshot(p, sm, phase_index(k, kPhDirop));
-            if (nact == 0) break;
-            partial = nact < p.n_sub;
+            if (active_snapshot(p, act_area<PR::kFull>(p, smem_base), phase_index(k, kPhDirop)) == 0) break;
         } else if (__ldcg(p.n_active) <= 0) {
             break;
         }
@@ -1302,7 +1325,9 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         cg_phase(kCtrRZ, k + 1, prolong_unit);
         if (!phase_end(p, 7, nts)) return;
     }
-    partial = false;
+    __syncthreads();
+    if (threadIdx.x == 0) g_partial_sh = 0;
+    __syncthreads();
     if constexpr (MX) {
         // closing FP64 coarse pressure correction (every instance is done;
         // the coarse phase runs in step-1 layout with a zero pressure part)
@@ -1760,6 +1785,17 @@ namespace bddc {
 
 size_t handle_device_bytes(const bddc_handle* h) { return h ? h->dev_bytes : 0; }
 
+// the persistent solve kernel for a precision, operator form and batch
+// (rebalanced over active instances when the batch has several)
+const void* solve_kernel_fn(int precision, int formulation, bool bal) {
+    if (precision == BDDC_PREC_FP32)
+        return bal ? (const void*)bddc_solve_kernel<PrecMixed, true> : (const void*)bddc_solve_kernel<PrecMixed, false>;
+    if (formulation == BDDC_FORM_FULL)
+        return bal ? (const void*)bddc_solve_kernel<PrecFP64Full, true>
+                   : (const void*)bddc_solve_kernel<PrecFP64Full, false>;
+    return bal ? (const void*)bddc_solve_kernel<PrecFP64, true> : (const void*)bddc_solve_kernel<PrecFP64, false>;
+}
+
 // device part of bddc_setup: upload a batch's host setup and size the launch
 int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_stream, Packed&& packed,
                       bddc_handle** out) {
@@ -1984,9 +2020,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         bddc_destroy(h);
         return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve
     }
-    const void* kfn = opt.precision == BDDC_PREC_FP32     ? (const void*)bddc_solve_kernel<PrecMixed>
-                      : opt.formulation == BDDC_FORM_FULL ? (const void*)bddc_solve_kernel<PrecFP64Full>
-                                                          : (const void*)bddc_solve_kernel<PrecFP64>;
+    const void* kfn = solve_kernel_fn(opt.precision, opt.formulation, p.act_n > 1);
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     int nb = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, h->smem);
@@ -2128,9 +2162,7 @@ int bddc_solve(bddc_handle* h, const double* f, const double* bc_value, double t
     cudaMemsetAsync(p.tstamp, 0, 2 * sizeof(long long) * (size_t)p.tstamp_cap, st);
     cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);
     void* args[] = {&p};
-    const void* kfn = h->precision == BDDC_PREC_FP32       ? (const void*)bddc_solve_kernel<PrecMixed>
-                      : h->formulation == BDDC_FORM_FULL ? (const void*)bddc_solve_kernel<PrecFP64Full>
-                                                         : (const void*)bddc_solve_kernel<PrecFP64>;
+    const void* kfn = solve_kernel_fn(h->precision, h->formulation, p.act_n > 1);
     cudaEventRecord(h->ev0, st);
     cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(h->grid), dim3(kThreads), args, h->smem, st);
     cudaEventRecord(h->ev1, st);
