@@ -424,13 +424,13 @@ __device__ __forceinline__ int act_find(const int* pre, int n, int64_t x) {
 }
 
 // stage x[0..n) as FP32 (hi only: inputs of the FP32 operators)
-__device__ __forceinline__ void split_hi(WarpSm& w, int n) {
+__device__ __forceinline__ void split_hi(WarpSm w, int n) {
     for (int k = threadIdx.x & 31; k < n; k += 32) w.xh[k] = __double2float_rn(w.x[k]);
     __syncwarp();
 }
 
 // stage x[0..n) from the warp's x into the FP32 pair representation
-__device__ __forceinline__ void split_pairs(WarpSm& w, int n) {
+__device__ __forceinline__ void split_pairs(WarpSm w, int n) {
     for (int k = threadIdx.x & 31; k < n; k += 32) {
         const double v = w.x[k];
         const float h = __double2float_rn(v);
@@ -449,7 +449,7 @@ __device__ __forceinline__ double to_double(float2 v) { return dd_dbl(v); }
 // restriction rc_a = sum_k P[a*ng + k] x[k]: lane per row a, walking its
 // contiguous row (consecutive loads of one lane share cache lines); all
 // loads are independent, so one pass costs about one memory latency
-__device__ __forceinline__ void restrict_rows(const double* __restrict__ P, int m, int ng, const WarpSm& w, double* out) {
+__device__ __forceinline__ void restrict_rows(const double* __restrict__ P, int m, int ng, const WarpSm w, double* out) {
     for (int a = threadIdx.x & 31; a < m; a += 32) {
         const double* row = P + (int64_t)a * ng;
         double a0 = 0.0, a1 = 0.0;
@@ -463,7 +463,7 @@ __device__ __forceinline__ void restrict_rows(const double* __restrict__ P, int 
         out[a] = a0 + a1;
     }
 }
-__device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m, int ng, const WarpSm& w, double* out,
+__device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m, int ng, const WarpSm w, double* out,
                                               const double* add = nullptr) {
     for (int a = threadIdx.x & 31; a < m; a += 32) {
         const float* row = P + (int64_t)a * ng;
@@ -480,12 +480,12 @@ __device__ __forceinline__ void restrict_rows(const float* __restrict__ P, int m
 }
 
 // prolongation value for output k: sum_a P[a*ng + k] wcs[a]
-__device__ __forceinline__ double prolong_out(const double* __restrict__ P, int m, int ng, const WarpSm& w, int k) {
+__device__ __forceinline__ double prolong_out(const double* __restrict__ P, int m, int ng, const WarpSm w, int k) {
     double acc = 0.0;
     for (int a = 0; a < m; ++a) acc = fma(__ldg(P + (int64_t)a * ng + k), w.wcs[a], acc);
     return acc;
 }
-__device__ __forceinline__ double prolong_out(const float* __restrict__ P, int m, int ng, const WarpSm& w, int k) {
+__device__ __forceinline__ double prolong_out(const float* __restrict__ P, int m, int ng, const WarpSm w, int k) {
     float acc = 0.0f;
     for (int a = 0; a < m; ++a) acc = fmaf(__ldg(P + (int64_t)a * ng + k), (float)w.wcs[a], acc);
     return (double)acc;
@@ -538,7 +538,7 @@ __device__ __forceinline__ void set_face_flux(const Params& p, int64_t s, double
     __syncwarp();
 }
 
-__device__ __forceinline__ void stage_wc(const Params& p, int64_t s, const double* wc_b, WarpSm& w) {
+__device__ __forceinline__ void stage_wc(const Params& p, int64_t s, const double* wc_b, WarpSm w) {
     const int m = p.sub_m[s];
     const int64_t co = p.off_cslot[s];
     for (int a = threadIdx.x & 31; a < m; a += 32) w.wcs[a] = __ldcg(wc_b + p.cslot_c[co + a]);
@@ -548,7 +548,7 @@ __device__ __forceinline__ void stage_wc(const Params& p, int64_t s, const doubl
 // subdomain correction and coarse restriction of the weighted residual in
 // w.x: yl = F x, rcl = Psi^T x (Algorithm 2 steps 1-2, local parts)
 template <class PR>
-__device__ void restrict_apply(const Params& p, int64_t s, WarpSm& w) {
+__device__ void restrict_apply(const Params& p, int64_t s, WarpSm w) {
     using F_t = typename PR::F_t;
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -575,7 +575,7 @@ __device__ void restrict_apply(const Params& p, int64_t s, WarpSm& w) {
 
 // ---- phases (warp per subdomain unless noted) --------------------------------------
 template <class PR>
-__device__ void ph_step1(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_step1(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -673,7 +673,7 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
 }
 
 template <class PR>
-__device__ void ph_u0(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_u0(const Params& p, int64_t s, WarpSm w) {
     using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s];
@@ -692,7 +692,7 @@ __device__ void ph_u0(const Params& p, int64_t s, WarpSm& w) {
 
 // Step 2 local residual r_G = S u_0 + G_pre f (stored in ql)
 template <class PR>
-__device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_step2(const Params& p, int64_t s, WarpSm w) {
     using S_t = typename PR::S_t;
     const int ng = p.sub_ng[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], cb = p.off_cell[s];
@@ -724,7 +724,7 @@ __device__ void ph_step2(const Params& p, int64_t s, WarpSm& w) {
 
 // f* = g - sum_i R_i^T r_G,i ; r_0 = f*, x_0 = 0 ; then restrict r_0
 template <class PR>
-__device__ void ph_fstar(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_fstar(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
     const int l = threadIdx.x & 31;
@@ -765,7 +765,7 @@ __device__ void ph_fstar(const Params& p, int64_t s, WarpSm& w) {
 // The CG phases store their partials and return false for an instance that
 // is done; the caller counts the arrivals (publish_total).
 template <class PR>
-__device__ bool ph_prolong(const Params& p, int64_t s, WarpSm& w) {
+__device__ bool ph_prolong(const Params& p, int64_t s, WarpSm w) {
     using F_t = typename PR::F_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
@@ -799,7 +799,7 @@ __device__ bool ph_prolong(const Params& p, int64_t s, WarpSm& w) {
 
 // direction update d = z + beta d and operator apply q = S d + B_0^T d_p
 template <class PR>
-__device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm w) {
     using S_t = typename PR::S_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
@@ -847,7 +847,7 @@ __device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
 // +p_K if the face is K's lower face, -p_K if its upper face.  Equal to
 // S^i d + d_s sigma p_0 up to rounding (the condensed form).
 template <class PR>
-__device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -905,7 +905,7 @@ __device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm& w) {
 }
 
 template <class PR>
-__device__ bool ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool ph_update(const Params& p, int64_t s, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -943,7 +943,7 @@ __device__ bool ph_update(const Params& p, int64_t s, int k, WarpSm& w) {
 
 // mixed path: FP64 restriction of the final residual for the closing coarse
 // pressure correction
-__device__ void ph_final_restrict(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_final_restrict(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -962,7 +962,7 @@ __device__ void ph_final_pressure(const Params& p, int64_t s) {
     p.xp[s] = __ldcg(p.xp + s) + __ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]);
 }
 
-__device__ void ph_post(const Params& p, int64_t s, WarpSm& w) {
+__device__ void ph_post(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s], ni = p.sub_ni[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], cb = p.off_cell[s], ib = p.off_int[s];
     const int l = threadIdx.x & 31;
@@ -1044,8 +1044,14 @@ __device__ void cs_rhs(const Params& p, bool step1) {
 // of 32 outputs, chunk) stores its partial sums; the unit whose arrival
 // completes a block sums the partials in chunk order (independent of the
 // arrival order) and writes the block.  A block with one chunk writes
-// directly.
-constexpr int kCsChunk = 64;
+// directly.  The chunk is fixed per node (not per batch), so an instance
+// gets the same bits alone and in a batch.
+//
+// A unit is latency-bound (a level has about one unit per warp), so it is
+// laid out for few dependent round trips: its record (CsUnit) in one load
+// batch; then the first half of its matrix chunk, the front indices and the
+// completion's indices together; then the right-hand-side values and the
+// children's updates together; then the second half of the matrix chunk.
 
 // the last of n arrivals at *cnt (whole warp; the completing warp resets it)
 __device__ __forceinline__ bool cs_arrive_last(int* cnt, int n) {
@@ -1060,99 +1066,110 @@ __device__ __forceinline__ bool cs_arrive_last(int* cnt, int n) {
     return last != 0;
 }
 
-// forward unit (node v, block cb of 32 boundary rows, chunk ic of its
-// pivots): t_i = b_i + children's updates for the chunk's pivots (stored
-// for the backward sweep by the units of block 0), partial (H^T t)_j over
-// the chunk; the block's u_j = children's updates - sum of the partials
-__device__ void cs_forward(const Params& p, int4 un) {
-    const int l = threadIdx.x & 31;
-    const int v = un.x, cb = un.y, ic = un.z;
-    const int b = p.cn_inst[v], pp = p.cn_p[v], q = p.cn_q[v];
-    const int64_t od = p.cn_off_dof[v], oh = p.cn_off_H[v], ou = p.cn_off_u[v], cs = p.inst_csoff[b];
-    const int nic = pp > 0 ? (pp + kCsChunk - 1) / kCsChunk : 1;
-    const int j = cb * 32 + l;
-    const int i_lo = ic * kCsChunk, i_hi = (i_lo + kCsChunk < pp) ? i_lo + kCsChunk : pp;
-    double acc = 0.0;
-    for (int i0 = i_lo; i0 < i_hi; i0 += 32) {
-        double tl = 0.0;
-        if (i0 + l < i_hi) {
-            const int64_t fi = od + i0 + l;
-            const int d = p.cn_dof[fi], c0 = p.cn_c0[fi], c1 = p.cn_c1[fi];
-            tl = __ldcg(p.cs_b + cs + d) + (c0 >= 0 ? __ldcg(p.cs_u + c0) : 0.0) + (c1 >= 0 ? __ldcg(p.cs_u + c1) : 0.0);
-            if (cb == 0) p.cs_t[cs + d] = tl;
-        }
-        const int ni = (i_hi - i0 < 32) ? i_hi - i0 : 32;
-        const double* Hr = p.cn_H + oh + (int64_t)i0 * q + j;
-#pragma unroll 8
-        for (int k = 0; k < ni; ++k) {
-            const double tk = __shfl_sync(0xffffffffu, tl, k);
-            if (j < q) acc = fma(__ldg(Hr + (int64_t)k * q), tk, acc);
-        }
-    }
-    if (q == 0) return;
-    if (nic > 1) {
-        double* part = p.cs_fpart + p.cn_fwp_off[v] + ((int64_t)cb * nic + ic) * 32;
-        part[l] = acc;
-        if (!cs_arrive_last(p.cs_fcnt + p.cn_fwc_off[v] + cb, nic)) return;
-        part = p.cs_fpart + p.cn_fwp_off[v] + (int64_t)cb * nic * 32;
-        acc = 0.0;
-        for (int c = 0; c < nic; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
-    }
-    if (j < q) {
-        const int64_t fj = od + pp + j;
-        const int c0 = p.cn_c0[fj], c1 = p.cn_c1[fj];
-        p.cs_u[ou + j] = (c0 >= 0 ? __ldcg(p.cs_u + c0) : 0.0) + (c1 >= 0 ? __ldcg(p.cs_u + c1) : 0.0) - acc;
-    }
+__device__ __forceinline__ CsUnit cs_load_unit(const CsUnit* u) {
+    CsUnit U;
+    const int4* src = reinterpret_cast<const int4*>(u);
+    int4* dst = reinterpret_cast<int4*>(&U);
+#pragma unroll
+    for (int t = 0; t < (int)(sizeof(CsUnit) / sizeof(int4)); ++t) dst[t] = __ldg(src + t);
+    return U;
 }
 
-// backward unit (node v, block rb of 32 pivot rows, chunk kc of the
+// acc += sum_{k < kh} m[k] * (value of column k, held by lane k of the warp)
+template <int kh>
+__device__ __forceinline__ double cs_dot(const double (&m)[kh], double v, int lane0, double acc) {
+    // lane0 + kh <= 32: the chunk has at most 32 terms, one per lane
+#pragma unroll
+    for (int k = 0; k < kh; ++k) acc = fma(m[k], __shfl_sync(0xffffffffu, v, lane0 + k), acc);
+    return acc;
+}
+
+// forward unit (node v, block of 32 boundary rows j, chunk of its pivots):
+// t_i = b_i + the children's updates for the chunk's pivots (stored for the
+// backward sweep by the units of block 0), partial (H^T t)_j over the
+// chunk; the block's u_j = children's updates - the sum of the partials
+__device__ void cs_forward(const Params& p, const CsUnit& U) {
+    constexpr int kh = 8;  // matrix entries in flight per lane
+    const int l = threadIdx.x & 31;
+    const int j = U.blk * 32 + l;
+    const int nk = U.k1 - U.k0;
+    const bool jin = j < U.q;
+    const double* Hc = p.cn_H + (int64_t)U.om + (int64_t)U.k0 * U.q + j;
+    double m[kh];
+#pragma unroll
+    for (int k = 0; k < kh; ++k) m[k] = (k < nk && jin) ? __ldg(Hc + (int64_t)k * U.q) : 0.0;
+    int4 ix = make_int4(-1, -1, -1, 0), jx = make_int4(-1, -1, -1, 0);
+    if (l < nk) ix = __ldg(p.cn_idx + (int64_t)U.od + U.k0 + l);
+    if (jin) jx = __ldg(p.cn_idx + (int64_t)U.od + U.pp + j);
+    double tl = 0.0, ch = 0.0;
+    if (l < nk) {
+        tl = __ldcg(p.cs_b + U.cs + ix.x) + (ix.y >= 0 ? __ldcg(p.cs_u + ix.y) : 0.0) +
+             (ix.z >= 0 ? __ldcg(p.cs_u + ix.z) : 0.0);
+        if (U.blk == 0) p.cs_t[U.cs + ix.x] = tl;
+    }
+    if (jin) ch = (jx.y >= 0 ? __ldcg(p.cs_u + jx.y) : 0.0) + (jx.z >= 0 ? __ldcg(p.cs_u + jx.z) : 0.0);
+    double acc = cs_dot(m, tl, 0, 0.0);
+    for (int k0 = kh; k0 < nk; k0 += kh) {
+#pragma unroll
+        for (int k = 0; k < kh; ++k) m[k] = (k0 + k < nk && jin) ? __ldg(Hc + (int64_t)(k0 + k) * U.q) : 0.0;
+        acc = cs_dot(m, tl, k0, acc);
+    }
+    if (U.q == 0) return;  // the root: only its t
+    if (U.nch > 1) {
+        double* part = p.cs_fpart + U.pof;
+        part[(int64_t)U.ich * 32 + l] = acc;
+        if (!cs_arrive_last(p.cs_fcnt + U.cof, U.nch)) return;
+        acc = 0.0;
+        for (int c = 0; c < U.nch; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
+    }
+    if (jin) p.cs_u[U.ou + j] = ch - acc;
+}
+
+// backward unit (node v, block of 32 pivot rows i, chunk of the
 // concatenated columns [P, B]): partial of x_i = sum_k X_ik t_k -
 // sum_j H_ij x_j (X symmetric: X_ik read as X[k][i]; H from its transpose);
 // the completed block goes to cs_x and, for the n_c + N coarse dofs, to wc
 template <class PR>
-__device__ void cs_backward(const Params& p, int4 un) {
+__device__ void cs_backward(const Params& p, const CsUnit& U) {
+    constexpr int kh = 8;  // matrix entries in flight per lane
     const int l = threadIdx.x & 31;
-    const int v = un.x, rb = un.y, kc = un.z;
-    const int b = p.cn_inst[v], pp = p.cn_p[v], q = p.cn_q[v];
-    const int64_t od = p.cn_off_dof[v], ox = p.cn_off_X[v], oh = p.cn_off_H[v], cs = p.inst_csoff[b];
-    const int nkc = (pp + q + kCsChunk - 1) / kCsChunk;
-    const int i = rb * 32 + l;
-    const int k_lo = kc * kCsChunk, k_hi = (k_lo + kCsChunk < pp + q) ? k_lo + kCsChunk : pp + q;
-    double acc = 0.0;
-    for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
-        // the column values: t at pivots (k < p), x at boundary dofs (k >= p)
-        double vl = 0.0;
-        if (k0 + l < k_hi) {
-            const int kk = k0 + l;
-            const double* src = kk < pp ? p.cs_t : p.cs_x;
-            vl = __ldcg(src + cs + p.cn_dof[od + kk]);
-        }
-        const int nk = (k_hi - k0 < 32) ? k_hi - k0 : 32;
-#pragma unroll 8
-        for (int k = 0; k < nk; ++k) {
-            const double vk = __shfl_sync(0xffffffffu, vl, k);
-            const int kk = k0 + k;
-            if (i < pp) {
-                const double c = kk < pp ? __ldg(p.cn_X + ox + (int64_t)kk * pp + i)
-                                         : -__ldg(p.cn_HT + oh + (int64_t)(kk - pp) * pp + i);
-                acc = fma(c, vk, acc);
-            }
-        }
+    const int i = U.blk * 32 + l;
+    const int nk = U.k1 - U.k0;
+    const bool iin = i < U.pp;
+    // column k of the chunk is kk = k0 + k: X row kk (kk < p), else -H^T row kk - p
+    auto mat = [&](int k) -> double {
+        const int kk = U.k0 + k;
+        if (k >= nk || !iin) return 0.0;
+        return kk < U.pp ? __ldg(p.cn_X + (int64_t)U.om + (int64_t)kk * U.pp + i)
+                         : -__ldg(p.cn_HT + (int64_t)U.ou + (int64_t)(kk - U.pp) * U.pp + i);
+    };
+    double m[kh];
+#pragma unroll
+    for (int k = 0; k < kh; ++k) m[k] = mat(k);
+    int dl = -1, di = -1;
+    if (l < nk) dl = __ldg(p.cn_idx + (int64_t)U.od + U.k0 + l).x;
+    if (iin) di = __ldg(p.cn_idx + (int64_t)U.od + i).x;
+    // the column values: t at pivots, x at boundary dofs (set one level up)
+    double vl = 0.0;
+    if (l < nk) vl = __ldcg((U.k0 + l < U.pp ? p.cs_t : p.cs_x) + U.cs + dl);
+    double acc = cs_dot(m, vl, 0, 0.0);
+    for (int k0 = kh; k0 < nk; k0 += kh) {
+#pragma unroll
+        for (int k = 0; k < kh; ++k) m[k] = mat(k0 + k);
+        acc = cs_dot(m, vl, k0, acc);
     }
-    if (nkc > 1) {
-        double* part = p.cs_bpart + p.cn_bwp_off[v] + ((int64_t)rb * nkc + kc) * 32;
-        part[l] = acc;
-        if (!cs_arrive_last(p.cs_bcnt + p.cn_bwc_off[v] + rb, nkc)) return;
-        part = p.cs_bpart + p.cn_bwp_off[v] + (int64_t)rb * nkc * 32;
+    if (U.nch > 1) {
+        double* part = p.cs_bpart + U.pof;
+        part[(int64_t)U.ich * 32 + l] = acc;
+        if (!cs_arrive_last(p.cs_bcnt + U.cof, U.nch)) return;
         acc = 0.0;
-        for (int c = 0; c < nkc; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
+        for (int c = 0; c < U.nch; ++c) acc += __ldcg(part + (int64_t)c * 32 + l);
     }
-    if (i < pp) {
-        const int d = p.cn_dof[od + i];
-        p.cs_x[cs + d] = acc;
-        if (d < p.inst_ncn[b]) {
-            if constexpr (PR::kMixed) reinterpret_cast<float2*>(p.wc)[p.inst_coff[b] + d] = dd_of(acc);
-            else p.wc[p.inst_coff[b] + d] = acc;
+    if (iin) {
+        p.cs_x[U.cs + di] = acc;
+        if (di < p.inst_ncn[U.b]) {
+            if constexpr (PR::kMixed) reinterpret_cast<float2*>(p.wc)[p.inst_coff[U.b] + di] = dd_of(acc);
+            else p.wc[p.inst_coff[U.b] + di] = acc;
         }
     }
 }
@@ -1167,11 +1184,21 @@ template <class PR, bool kBal>
 __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     constexpr bool MX = PR::kMixed;
     extern __shared__ double smem_base[];
-    CtaSm sm = carve<PR::kFull>(p, smem_base);
-    WarpSm& w = sm.w;
+    // the shared-memory areas are formed where a unit uses them, so that no
+    // register holds their addresses across the phases (the kernel runs at
+    // its register cap); the CTA's coarse right-hand side starts the area
+    auto wsm = [&]() { return carve<PR::kFull>(p, smem_base).w; };
     int64_t a, e;
     int staged;
     int nts = 0;
+    // sparse coarse solve: the first unit of every depth, forward then backward
+    __shared__ int64_t cs_lvl[2 * (kCsMaxLevels + 1)];
+    if (p.coarse_sparse && p.cn_levels <= kCsMaxLevels)
+        for (int d = threadIdx.x; d <= p.cn_levels; d += kThreads) {
+            cs_lvl[d] = p.fw_off[d];
+            cs_lvl[kCsMaxLevels + 1 + d] = p.bw_off[d];
+        }
+    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.tstamp && p.tstamp_cap > 0) {
         long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1201,8 +1228,8 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
                 const int b = act_find(act_cu, p.act_n, x);
                 u = p.inst_cu0[b] + (x - act_cu[b]);
             }
-            if constexpr (MX) mx_coarse(p, u, step1, sm.rhs, staged);
-            else ph_coarse<PR>(p, u, step1, sm.rhs, staged);
+            if constexpr (MX) mx_coarse(p, u, step1, smem_base, staged);
+            else ph_coarse<PR>(p, u, step1, smem_base, staged);
         }
     };
     // a coarse solve and the grid barrier(s) after it: the dense inverse in
@@ -1216,21 +1243,24 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         }
         cs_rhs<PR>(p, step1);
         if (!phase_end(p, id, nts)) return false;
+        // the unit offsets per depth: from shared memory (staged at the start)
+        // when the tree is not deeper than kCsMaxLevels
+        const bool lvl_sh = p.cn_levels <= kCsMaxLevels;
         for (int d = p.cn_levels - 1; d >= 0; --d) {
-            const int64_t u0 = p.fw_off[d];
-            warp_range(p.fw_off[d + 1] - u0, a, e);
+            const int64_t u0 = lvl_sh ? cs_lvl[d] : p.fw_off[d];
+            warp_range((lvl_sh ? cs_lvl[d + 1] : p.fw_off[d + 1]) - u0, a, e);
             for (int64_t u = a; u < e; ++u) {
-                const int4 un = p.fw_unit[u0 + u];
-                if (step1 || !inst_done(p, p.cn_inst[un.x])) cs_forward(p, un);
+                const CsUnit U = cs_load_unit(p.fw_unit + u0 + u);
+                if (step1 || p.n_inst == 1 || !inst_done(p, U.b)) cs_forward(p, U);
             }
             if (!phase_end(p, id, nts)) return false;
         }
         for (int d = 0; d < p.cn_levels; ++d) {
-            const int64_t u0 = p.bw_off[d];
-            warp_range(p.bw_off[d + 1] - u0, a, e);
+            const int64_t u0 = lvl_sh ? cs_lvl[kCsMaxLevels + 1 + d] : p.bw_off[d];
+            warp_range((lvl_sh ? cs_lvl[kCsMaxLevels + 2 + d] : p.bw_off[d + 1]) - u0, a, e);
             for (int64_t u = a; u < e; ++u) {
-                const int4 un = p.bw_unit[u0 + u];
-                if (step1 || !inst_done(p, p.cn_inst[un.x])) cs_backward<PR>(p, un);
+                const CsUnit U = cs_load_unit(p.bw_unit + u0 + u);
+                if (step1 || p.n_inst == 1 || !inst_done(p, U.b)) cs_backward<PR>(p, U);
             }
             if (!phase_end(p, id, nts)) return false;
         }
@@ -1238,22 +1268,22 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     };
     sub_range(p, a, e);
     for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_step1(p, s, w);
-        else ph_step1<PR>(p, s, w);
+        if constexpr (MX) mx_step1(p, s, wsm());
+        else ph_step1<PR>(p, s, wsm());
     }
     if (!phase_end(p, 1, nts)) return;
     if (!coarse_solve(true, 2)) return;
     sub_range(p, a, e);
     for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_u0(p, s, w);
-        else ph_u0<PR>(p, s, w);
+        if constexpr (MX) mx_u0(p, s, wsm());
+        else ph_u0<PR>(p, s, wsm());
     }
     if (!phase_end(p, 3, nts)) return;
-    for (int64_t s = a; s < e; ++s) ph_step2<PR>(p, s, w);
+    for (int64_t s = a; s < e; ++s) ph_step2<PR>(p, s, wsm());
     if (!phase_end(p, 4, nts)) return;
     for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_fstar(p, s, w);
-        else ph_fstar<PR>(p, s, w);
+        if constexpr (MX) mx_fstar(p, s, wsm());
+        else ph_fstar<PR>(p, s, wsm());
     }
     if (!phase_end(p, 5, nts)) return;
     if (!coarse_solve(false, 6)) return;
@@ -1295,8 +1325,8 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     };
     // each PROLONG ends with the convergence test of the next iteration
     auto prolong_unit = [&](int64_t s) -> bool {
-        if constexpr (MX) return mx_prolong(p, s, w);
-        else return ph_prolong<PR>(p, s, w);
+        if constexpr (MX) return mx_prolong(p, s, wsm());
+        else return ph_prolong<PR>(p, s, wsm());
     };
     cg_phase(kCtrRZ, 0, prolong_unit);
     if (!phase_end(p, 7, nts)) return;
@@ -1311,14 +1341,14 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
             break;
         }
         cg_phase(kCtrDQ, k, [&](int64_t s) -> bool {
-            if constexpr (MX) return mx_dirop(p, s, k, w);
-            else if constexpr (PR::kFull) return ph_dirop_full<PR>(p, s, k, w);
-            else return ph_dirop<PR>(p, s, k, w);
+            if constexpr (MX) return mx_dirop(p, s, k, wsm());
+            else if constexpr (PR::kFull) return ph_dirop_full<PR>(p, s, k, wsm());
+            else return ph_dirop<PR>(p, s, k, wsm());
         });
         if (!phase_end(p, 8, nts)) return;
         cg_phase(kCtrRR, k, [&](int64_t s) -> bool {
-            if constexpr (MX) return mx_update(p, s, k, w);
-            else return ph_update<PR>(p, s, k, w);
+            if constexpr (MX) return mx_update(p, s, k, wsm());
+            else return ph_update<PR>(p, s, k, wsm());
         });
         if (!phase_end(p, 9, nts)) return;
         if (!coarse_solve(false, 6)) return;
@@ -1332,7 +1362,7 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         // closing FP64 coarse pressure correction (every instance is done;
         // the coarse phase runs in step-1 layout with a zero pressure part)
         sub_range(p, a, e);
-        for (int64_t s = a; s < e; ++s) mx_final_restrict(p, s, w);
+        for (int64_t s = a; s < e; ++s) mx_final_restrict(p, s, wsm());
         if (!phase_end(p, 10, nts)) return;
         cta_range(p.n_sub, a, e);
         for (int64_t s = a; s < e; ++s)
@@ -1345,8 +1375,8 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
     }
     sub_range(p, a, e);
     for (int64_t s = a; s < e; ++s) {
-        if constexpr (MX) mx_post(p, s, w);
-        else ph_post(p, s, w);
+        if constexpr (MX) mx_post(p, s, wsm());
+        else ph_post(p, s, wsm());
     }
 }
 
@@ -1419,14 +1449,14 @@ __global__ void __launch_bounds__(kThreads) k_cs_rhs(Params p) {
 __global__ void __launch_bounds__(kThreads) k_cs_forward(Params p, int d) {
     const int64_t W = (int64_t)gridDim.x * kWarps, u0 = p.fw_off[d], nu = p.fw_off[d + 1] - u0;
     for (int64_t u = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); u < nu; u += W) {
-        cs_forward(p, p.fw_unit[u0 + u]);
+        cs_forward(p, cs_load_unit(p.fw_unit + u0 + u));
     }
 }
 template <class PR>
 __global__ void __launch_bounds__(kThreads) k_cs_backward(Params p, int d) {
     const int64_t W = (int64_t)gridDim.x * kWarps, u0 = p.bw_off[d], nu = p.bw_off[d + 1] - u0;
     for (int64_t u = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); u < nu; u += W) {
-        cs_backward<PR>(p, p.bw_unit[u0 + u]);
+        cs_backward<PR>(p, cs_load_unit(p.bw_unit + u0 + u));
     }
 }
 
@@ -1876,34 +1906,66 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     if (!rc && P.coarse_sparse) {
         // multifrontal coarse factor and its work units per tree depth
         p.coarse_sparse = 1;
-        UP(inst_csoff, P.inst_csoff); UP(cn_inst, P.cn_inst); UP(cn_p, P.cn_p); UP(cn_q, P.cn_q);
-        UP(cn_dof, P.cn_dof); UP(cn_c0, P.cn_c0); UP(cn_c1, P.cn_c1);
-        UP(cn_off_dof, P.cn_off_dof); UP(cn_off_X, P.cn_off_X); UP(cn_off_H, P.cn_off_H); UP(cn_off_u, P.cn_off_u);
+        UP(inst_csoff, P.inst_csoff);
         UP(cn_X, P.cn_X); UP(cn_H, P.cn_H); UP(cn_HT, P.cn_HT);
         const int L = P.cn_max_depth + 1;
         const size_t nn = P.cn_p.size();
-        std::vector<std::vector<int4>> fw(L), bw(L);
+        // the sweep units hold 32-bit offsets
+        const int64_t kLim = (int64_t)1 << 31;
+        if ((int64_t)P.cn_X.size() >= kLim || (int64_t)P.cn_H.size() >= kLim || (int64_t)P.cn_dof.size() >= kLim ||
+            P.n_csys >= kLim || P.n_cu >= kLim) {
+            bddc_destroy(h);
+            return BDDC_E_INVALID_ARG;  // coarse factor too large for one handle
+        }
+        // per front position: (dof, c0, c1, -)
+        {
+            std::vector<int4> idx(P.cn_dof.size());
+            for (size_t q = 0; q < idx.size(); ++q) idx[q] = make_int4(P.cn_dof[q], P.cn_c0[q], P.cn_c1[q], 0);
+            UP(cn_idx, idx);
+        }
+        std::vector<std::vector<CsUnit>> fw(L), bw(L);
         std::vector<int64_t> fwc(nn), fwp(nn), bwc(nn), bwp(nn);
         int64_t nfc = 0, nfp = 0, nbc = 0, nbp = 0;
         for (size_t v = 0; v < nn; ++v) {
-            const int d = P.cn_depth[v], pp = P.cn_p[v], q = P.cn_q[v];
+            const int d = P.cn_depth[v], pp = P.cn_p[v], q = P.cn_q[v], b = P.cn_inst[v];
             const int ncb = std::max(1, (q + 31) / 32), nic = pp > 0 ? (pp + kCsChunk - 1) / kCsChunk : 1;
             const int nrb = (pp + 31) / 32, nkc = (pp + q + kCsChunk - 1) / kCsChunk;
-            for (int cb = 0; cb < ncb; ++cb)
-                for (int ic = 0; ic < nic; ++ic) fw[d].push_back(make_int4((int)v, cb, ic, 0));
-            for (int rb = 0; rb < nrb; ++rb)
-                for (int kc = 0; kc < nkc; ++kc) bw[d].push_back(make_int4((int)v, rb, kc, 0));
             fwc[v] = nfc; nfc += ncb;
             fwp[v] = nfp; nfp += (int64_t)ncb * nic * 32;
             bwc[v] = nbc; nbc += nrb;
             bwp[v] = nbp; nbp += (int64_t)nrb * nkc * 32;
+            CsUnit U{};
+            U.pp = pp; U.q = q; U.b = b;
+            U.od = (int)P.cn_off_dof[v];
+            U.cs = (int)P.inst_csoff[b];
+            for (int cb = 0; cb < ncb; ++cb)
+                for (int ic = 0; ic < nic; ++ic) {
+                    U.blk = cb; U.ich = ic; U.nch = nic;
+                    U.k0 = std::min(pp, ic * kCsChunk);
+                    U.k1 = std::min(pp, U.k0 + kCsChunk);
+                    U.om = (int)P.cn_off_H[v];
+                    U.ou = (int)P.cn_off_u[v];
+                    U.pof = (int)(fwp[v] + (int64_t)cb * nic * 32);
+                    U.cof = (int)(fwc[v] + cb);
+                    fw[d].push_back(U);
+                }
+            for (int rb = 0; rb < nrb; ++rb)
+                for (int kc = 0; kc < nkc; ++kc) {
+                    U.blk = rb; U.ich = kc; U.nch = nkc;
+                    U.k0 = kc * kCsChunk;
+                    U.k1 = std::min(pp + q, U.k0 + kCsChunk);
+                    U.om = (int)P.cn_off_X[v];
+                    U.ou = (int)P.cn_off_H[v];
+                    U.pof = (int)(bwp[v] + (int64_t)rb * nkc * 32);
+                    U.cof = (int)(bwc[v] + rb);
+                    bw[d].push_back(U);
+                }
         }
-        UP(cn_fwc_off, fwc); UP(cn_fwp_off, fwp); UP(cn_bwc_off, bwc); UP(cn_bwp_off, bwp);
         if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nfc, 1), &p.cs_fcnt);
         if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nbc, 1), &p.cs_bcnt);
         if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nfp, 1), &p.cs_fpart);
         if (!rc) rc = dalloc(h, (size_t)std::max<int64_t>(nbp, 1), &p.cs_bpart);
-        std::vector<int4> fu, bu;
+        std::vector<CsUnit> fu, bu;
         std::vector<int64_t> fo(1, 0), bo(1, 0);
         for (int d = 0; d < L; ++d) {
             fu.insert(fu.end(), fw[d].begin(), fw[d].end());

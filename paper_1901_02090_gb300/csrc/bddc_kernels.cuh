@@ -33,6 +33,26 @@ constexpr int kCoarseRows = 16;             // coarse rows per work unit
 constexpr long long kBarrierWaitNs = 10000000000LL;  // a grid-barrier wait past 10 s is an error
 constexpr int kActMaxInst = 4096;           // largest batch whose CG phases are rebalanced over active instances
 
+// A unit of the sparse coarse solve's sweeps (built on the host): node v,
+// block blk of 32 outputs (boundary rows of H^T t in the forward sweep, pivot
+// rows of x in the backward sweep) and the chunk [k0, k1) of its dot
+// products (pivots forward; the concatenated columns [P, B] backward), with
+// every offset the unit reads, so that one 64-byte record (four 16-byte
+// loads) starts it.  The offsets are 32-bit: the setup rejects a factor or
+// a coarse system past 2^31 entries for the sparse solver.
+struct __align__(16) CsUnit {
+    int blk, k0, k1, b;    // output block, chunk, instance
+    int pp, q, nch, ich;   // the node's pivots and boundary, chunks of the block, this chunk
+    int od;                // front dofs of the node (cn_idx)
+    int om;                // the chunk's matrix: H (forward) or X (backward)
+    int ou;                // the node's update vector in cs_u (forward) or H^T (backward)
+    int cs;                // the instance's coarse system vectors
+    int pof, cof;          // the block's partial sums and arrival counter
+    int pad0, pad1;
+};
+constexpr int kCsChunk = 32;  // terms of a unit's dot products
+constexpr int kCsMaxLevels = 62;  // tree depths whose unit offsets are staged in shared memory
+
 struct GridSync {
     unsigned int count;
     unsigned int gen;
@@ -113,24 +133,20 @@ struct Params {
     double *alpha_hist, *beta_hist, *rho_hist;                 // n_inst x (maxit + 1)
     int* n_active;
     GridSync* gsync;
-    // sparse coarse solver (coarse_sparse = 1, bddc_coarse.cpp): per node of
-    // every instance's dissection tree p, q, the offsets of its front dofs
-    // (P then B, instance-local), of X (p x p, symmetric), H (p x q), HT
-    // (q x p) and of its update vector in cs_u; per front position the cs_u
-    // index of each child's update for that dof (-1: none).  Work units per
-    // tree depth: forward (blocks of 32 B rows of H^T t) and backward (blocks
-    // of 32 P rows of x), each split into chunks of its dot products, with
-    // prefix offsets per depth.
+    // sparse coarse solver (coarse_sparse = 1, bddc_coarse.cpp): the
+    // multifrontal factor of every instance's coarse problem, per node X
+    // (p x p, symmetric), H (p x q) and H^T (q x p); per front position its
+    // dof and the children's update entries (cn_idx); the coarse system
+    // vectors (right-hand side b, forward values t, solution x, the nodes'
+    // update vectors u); the sweep units per tree depth (fw_off, bw_off:
+    // prefix offsets) with their partial sums and arrival counters
     int coarse_sparse, cn_levels;
     const int64_t* inst_csoff;
-    const int *cn_inst, *cn_p, *cn_q, *cn_dof, *cn_c0, *cn_c1;
-    const int64_t *cn_off_dof, *cn_off_X, *cn_off_H, *cn_off_u;
     const double *cn_X, *cn_H, *cn_HT;
     double *cs_b, *cs_t, *cs_x, *cs_u;
     const int64_t *fw_off, *bw_off;
-    const int4 *fw_unit, *bw_unit;  // (node, block of 32 outputs, chunk of the dot products, -)
-    // per node: offsets of its blocks' arrival counters and partial sums
-    const int64_t *cn_fwc_off, *cn_fwp_off, *cn_bwc_off, *cn_bwp_off;
+    const CsUnit *fw_unit, *bw_unit;
+    const int4* cn_idx;  // per front position: (instance-local dof, children's update indices c0, c1, -)
     int *cs_fcnt, *cs_bcnt;
     double *cs_fpart, *cs_bpart;
     // phase timestamps (CTA 0 at each barrier): pairs (phase id, ns)

@@ -37,7 +37,7 @@ __device__ __forceinline__ void mx_face_means(const Params& p, int64_t s, const 
 
 // local part of Algorithm 2 for the weighted residual held in (w.xh, w.xl):
 // rc = Psi_0^T r + Psi^T P_Z r, y = P_Z F P_Z r
-__device__ void mx_restrict(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_restrict(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
     const int l = threadIdx.x & 31;
@@ -94,7 +94,7 @@ __device__ void mx_restrict(const Params& p, int64_t s, WarpSm& w) {
 
 // v = Psi_0 wcs + P_Z Psi wcs for the staged coarse values (w.wcs as pairs);
 // the result is left in (w.xh, w.xl)
-__device__ void mx_prolong_local(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_prolong_local(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
     const int l = threadIdx.x & 31;
@@ -122,7 +122,7 @@ __device__ void mx_prolong_local(const Params& p, int64_t s, WarpSm& w) {
     __syncwarp();
 }
 
-__device__ __forceinline__ void mx_stage_wc(const Params& p, int64_t s, const float2* wc_b, WarpSm& w) {
+__device__ __forceinline__ void mx_stage_wc(const Params& p, int64_t s, const float2* wc_b, WarpSm w) {
     const int m = p.sub_m[s];
     const int64_t co = p.off_cslot[s];
     float2* wcs = V2(w.wcs);
@@ -131,7 +131,7 @@ __device__ __forceinline__ void mx_stage_wc(const Params& p, int64_t s, const fl
 }
 
 // ---- phases ------------------------------------------------------------------------------
-__device__ void mx_step1(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_step1(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -214,7 +214,7 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
     }
 }
 
-__device__ void mx_u0(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_u0(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
@@ -226,7 +226,7 @@ __device__ void mx_u0(const Params& p, int64_t s, WarpSm& w) {
 }
 
 // f* (FP64, once per solve), r_0 = f* and x_0 = 0 as pairs, then restrict r_0
-__device__ void mx_fstar(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_fstar(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s];
     const int64_t so = p.off_slot[s];
     const int l = threadIdx.x & 31;
@@ -268,7 +268,7 @@ __device__ void mx_fstar(const Params& p, int64_t s, WarpSm& w) {
     mx_restrict(p, s, w);
 }
 
-__device__ bool mx_prolong(const Params& p, int64_t s, WarpSm& w) {
+__device__ bool mx_prolong(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int ng = p.sub_ng[s];
@@ -295,7 +295,7 @@ __device__ bool mx_prolong(const Params& p, int64_t s, WarpSm& w) {
 }
 
 // direction update and operator apply (pairs)
-__device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -336,7 +336,7 @@ __device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm& w) {
     return true;
 }
 
-__device__ bool mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
+__device__ bool mx_update(const Params& p, int64_t s, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -380,7 +380,7 @@ __device__ bool mx_update(const Params& p, int64_t s, int k, WarpSm& w) {
 
 // closing FP64 coarse pressure correction: FP64 restriction of the final
 // residual (stored as pairs), coarse solve, x_p += p_0
-__device__ void mx_final_restrict(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_final_restrict(const Params& p, int64_t s, WarpSm w) {
     const int b = p.sub_inst[s];
     const int ng = p.sub_ng[s], m = p.sub_m[s];
     const int64_t so = p.off_slot[s], co = p.off_cslot[s];
@@ -406,7 +406,7 @@ __device__ void mx_final_pressure(const Params& p, int64_t s) {
     p.xp[s] = __ldcg(p.xp + s) + dd_dbl(__ldcg(wcb + p.inst_ncf[b] + p.sub_local[s]));
 }
 
-__device__ void mx_post(const Params& p, int64_t s, WarpSm& w) {
+__device__ void mx_post(const Params& p, int64_t s, WarpSm w) {
     const int ng = p.sub_ng[s], ni = p.sub_ni[s], nc = p.sub_nc[s];
     const int64_t so = p.off_slot[s], cb = p.off_cell[s], ib = p.off_int[s];
     const int l = threadIdx.x & 31;
