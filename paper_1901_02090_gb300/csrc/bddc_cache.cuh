@@ -30,3 +30,21 @@ __device__ __forceinline__ float2 ld_hint(const float2* ptr, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol));
     return v;
 }
+
+// L2 prefetch of the 128-byte line holding ptr.  A prefetch only warms L2:
+// the data still arrives through the normal loads, which then hit L2
+// instead of waiting for DRAM.  The sparse coarse sweeps use it for a
+// unit's matrix rows, whose loads it issues in batches of 8 (the kernel's
+// register cap).  (A bulk prefetch of the subdomain operator blocks at the
+// start of a unit was measured slower: their loads follow at once.)
+__device__ __forceinline__ void prefetch_l2_line(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+// the lines of n consecutive doubles from ptr (n <= 32): elements 0, 16 and
+// n - 1 lie on every line the range touches
+__device__ __forceinline__ void prefetch_l2_row32(const double* ptr, int n) {
+    if (n <= 0) return;
+    prefetch_l2_line(ptr);
+    if (n > 16) prefetch_l2_line(ptr + 16);
+    prefetch_l2_line(ptr + n - 1);
+}

@@ -1095,6 +1095,8 @@ __device__ void cs_forward(const Params& p, const CsUnit& U) {
     const int nk = U.k1 - U.k0;
     const bool jin = j < U.q;
     const double* Hc = p.cn_H + (int64_t)U.om + (int64_t)U.k0 * U.q + j;
+    if (l < nk && U.q > U.blk * 32)
+        prefetch_l2_row32(p.cn_H + (int64_t)U.om + (int64_t)(U.k0 + l) * U.q + U.blk * 32, min(32, U.q - U.blk * 32));
     double m[kh];
 #pragma unroll
     for (int k = 0; k < kh; ++k) m[k] = (k < nk && jin) ? __ldg(Hc + (int64_t)k * U.q) : 0.0;
@@ -1143,6 +1145,12 @@ __device__ void cs_backward(const Params& p, const CsUnit& U) {
         return kk < U.pp ? __ldg(p.cn_X + (int64_t)U.om + (int64_t)kk * U.pp + i)
                          : -__ldg(p.cn_HT + (int64_t)U.ou + (int64_t)(kk - U.pp) * U.pp + i);
     };
+    if (l < nk && U.pp > U.blk * 32) {
+        const int kk = U.k0 + l;
+        prefetch_l2_row32(kk < U.pp ? p.cn_X + (int64_t)U.om + (int64_t)kk * U.pp + U.blk * 32
+                                    : p.cn_HT + (int64_t)U.ou + (int64_t)(kk - U.pp) * U.pp + U.blk * 32,
+                          min(32, U.pp - U.blk * 32));
+    }
     double m[kh];
 #pragma unroll
     for (int k = 0; k < kh; ++k) m[k] = mat(k);
