@@ -335,15 +335,16 @@ void bddc_destroy(bddc_handle* h);
  * a stream of independent problems of any sizes.
  *
  * bddc_submit copies a request (host arrays) and returns a ticket at once.
- * A setup thread takes the requests in arrival order (consecutive requests
- * with equal tol, at most max_batch), runs their host setup (Algorithm 3 and
- * the local maps), admits the batch when its device footprint fits the HBM
- * budget beside the batches already on the device, and uploads it.  A solve
- * thread runs the admitted batches on the GPU one after another (one launch
- * of the persistent kernel each).  The host setup and the upload of the next
- * batch overlap the solve of the current one, and requests that arrive while
- * a batch is on the GPU join the next batch.  Results are collected by ticket
- * with bddc_poll (and waited for with bddc_wait).
+ * Two setup threads take the requests in arrival order (consecutive requests
+ * with equal tol, at most max_batch per batch), run their setup (Algorithm 3
+ * and the local maps; the dense parts on the GPU), admit a batch when its
+ * device footprint fits the HBM budget beside the batches already on the
+ * device, and upload it.  A solve thread runs the admitted batches on the
+ * GPU one after another (one launch of the persistent kernel each).  The
+ * setups of two batches overlap each other (one on the host while the other
+ * is on the GPU) and the solve of the current batch; requests that arrive
+ * while batches are being set up or solved join a later batch.  Results are
+ * collected by ticket with bddc_poll (and waited for with bddc_wait).
  *
  * The result of a request is bitwise the same as bddc_setup + bddc_solve of
  * that problem alone with the same options: the kernel's arithmetic for one

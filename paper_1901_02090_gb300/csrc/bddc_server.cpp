@@ -1,8 +1,8 @@
 // Serving loop over the batch solver: continuous batching of independent
 // solves (the request API of include/bddc.h).
 //
-// Two host threads per server:
-//   setup thread  takes the queued requests in arrival order (consecutive
+// Host threads per server (kSetupThreads + 1):
+//   setup threads take the queued requests in arrival order (consecutive
 //                 requests with equal tol, at most max_batch), runs the
 //                 setup of the batch (bddc::build_all, the dense local maps
 //                 on the GPU), waits until the
@@ -13,10 +13,15 @@
 //                 the persistent kernel each), copies every request's slice
 //                 of the results, frees the batch and returns its memory to
 //                 the budget.
-// While a batch is solved the next one is set up and uploaded, and requests
-// arriving meanwhile join the batch after it.  Uploads use the legacy default
-// stream with synchronous copies; solves run on the server's non-blocking
-// stream, so the two overlap on the device.
+// While a batch is solved the next ones are set up and uploaded, and requests
+// arriving meanwhile join a later batch.  Two setup threads work on two
+// batches at once: the setup of a batch alternates between GPU-bound stages
+// (the dense local maps and the face eigenproblems, FP64 on the device) and
+// host-bound ones (constraints, correction maps, coarse inverse, packing), so
+// one batch's host stages overlap the other's device stages.  Uploads use the
+// legacy default stream with synchronous copies; solves run on the server's
+// non-blocking stream, so they overlap on the device.  A batch that finishes
+// its setup first is solved first; results are collected by ticket.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -133,7 +138,8 @@ struct bddc_server {
     int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_batches = 0;
     int solving = 0;                // batches popped by the solve thread, not yet finished
     bool stop = false;
-    std::thread setup_thr, solve_thr;
+    static constexpr int kSetupThreads = 2;
+    std::thread setup_thr[kSetupThreads], solve_thr;
 };
 
 namespace {
@@ -357,7 +363,7 @@ int bddc_server_create(const bddc_options* opt_in, size_t hbm_budget_bytes, int 
         delete s;
         return BDDC_E_CUDA;
     }
-    s->setup_thr = std::thread(setup_loop, s);
+    for (std::thread& t : s->setup_thr) t = std::thread(setup_loop, s);
     s->solve_thr = std::thread(solve_loop, s);
     *out = s;
     return BDDC_OK;
@@ -448,7 +454,8 @@ void bddc_server_destroy(bddc_server* s) {
         s->queue.clear();
         s->cv.notify_all();
     }
-    if (s->setup_thr.joinable()) s->setup_thr.join();
+    for (std::thread& t : s->setup_thr)
+        if (t.joinable()) t.join();
     if (s->solve_thr.joinable()) s->solve_thr.join();
     for (Batch& b : s->ready)  // admitted after the solve thread stopped: not solved
         if (b.h) bddc_destroy(b.h);
