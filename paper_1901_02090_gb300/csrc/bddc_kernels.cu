@@ -1747,6 +1747,28 @@ int dalloc(bddc_handle* h, size_t n, T** out) {
     return BDDC_OK;
 }
 
+// Raise, never lower, a kernel's limit of dynamic shared memory.  The limit
+// is one value per kernel for the whole process, and handles of different
+// sizes are set up on several host threads (the serving loop) while earlier
+// handles launch: lowering it for a small batch would make the launch of a
+// larger one fail.
+std::mutex g_smem_mu;
+std::vector<std::pair<const void*, size_t>> g_smem_max;
+bool ensure_smem(const void* fn, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    for (auto& e : g_smem_max)
+        if (e.first == fn) {
+            if (e.second >= bytes) return true;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+                return false;
+            e.second = bytes;
+            return true;
+        }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+    g_smem_max.emplace_back(fn, bytes);
+    return true;
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -2091,7 +2113,18 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve
     }
     const void* kfn = solve_kernel_fn(opt.precision, opt.formulation, p.act_n > 1);
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    // the stand-alone operator / preconditioner kernels use the same carve
+    const void* aux[] = {(const void*)k_operator_local<PrecFP64>, (const void*)k_operator_local<PrecMixed>,
+                         (const void*)k_precond_restrict<PrecFP64>, (const void*)k_precond_restrict<PrecMixed>,
+                         (const void*)k_precond_coarse<PrecFP64>, (const void*)k_precond_coarse<PrecMixed>,
+                         (const void*)k_precond_prolong<PrecFP64>, (const void*)k_precond_prolong<PrecMixed>};
+    bool attr_ok = ensure_smem(kfn, h->smem);
+    for (const void* f : aux) attr_ok = attr_ok && ensure_smem(f, h->smem);
+    if (!attr_ok) {
+        cudaGetLastError();
+        bddc_destroy(h);
+        return BDDC_E_CUDA;
+    }
     int nb = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, h->smem);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
