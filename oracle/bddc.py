@@ -151,9 +151,15 @@ class BDDCOracle:
         (face-average) constraints only.
     scaling : "multiplicity" (default, Sec. 5) or "stiffness".
     pressure_scaling : apply the block rescaling D of Sec. 4.
+    constraints : None (the initial net-flux constraints, plus Algorithm 3
+        when tau is given), "msmfem" (plus one MsMFEM row per face, the
+        comparison method of Sec. 5; tau is ignored) or "explicit" (plus the
+        rows of ``explicit_rows``: a list of (global face ids, coefficients),
+        each on one face).
     """
 
-    def __init__(self, problem, tau=None, scaling="multiplicity", pressure_scaling=True):
+    def __init__(self, problem, tau=None, scaling="multiplicity", pressure_scaling=True, constraints=None,
+                 explicit_rows=None):
         self.problem = problem
         self.disc = Discretization(problem)
         self.ss = Substructuring(self.disc, problem.partition, scaling=scaling,
@@ -161,6 +167,17 @@ class BDDCOracle:
         self.tau = tau
         self.omega_tilde = None
         self.face_eigenvalues = None
+        if constraints in ("msmfem", "explicit"):
+            from .msmfem import explicit_constraints, msmfem_constraints
+            rows = msmfem_constraints(self) if constraints == "msmfem" else \
+                explicit_constraints(self, explicit_rows or [])
+            for fidx, new_rows in sorted(rows.items()):
+                self.ss.add_face_rows(fidx, new_rows)
+            self.n_added = sum(len(r) for r in rows.values())
+            self._build(initial=False)
+            return
+        if constraints is not None:
+            raise ValueError(f"unknown constraints {constraints!r}")
         self._build(initial=True)
         if tau is not None and np.isfinite(tau):
             from .adaptive import adaptive_constraints
