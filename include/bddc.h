@@ -74,6 +74,28 @@ extern "C" {
 #define BDDC_SCALING_MULTIPLICITY 0
 #define BDDC_SCALING_STIFFNESS 1
 
+/* Constraint set: the flux coarse dofs of each face Gamma^{ij} between two
+ * subdomains (Sec. 3.1, eq. (C^i)).  All modes start from the initial
+ * net-flux constraint of every face (Assumption 1) and add rows per face,
+ * orthonormalised against the face's rows (a row in their span adds
+ * nothing):
+ *   ADAPTIVE  the rows of Algorithm 3 when tau > 0 (the method; tau <= 0:
+ *             the initial constraints alone);
+ *   MSMFEM    one row per face, the comparison method of Sec. 5: the flux on
+ *             the face dofs of the local Darcy problem on the face's pair of
+ *             subdomains with the sources 1/|Omega^i| on Omega^i and
+ *             -1/|Omega^j| on Omega^j and no flow through the pair's
+ *             boundary (the setup has no sources, so the uniform
+ *             distribution is used in every subdomain; well-weighted rows
+ *             can be given as EXPLICIT rows); tau is ignored;
+ *   EXPLICIT  the caller's rows (bddc_instance.n_rows ...); tau is ignored.
+ * bddc_stats.n_adaptive counts the rows added by any mode; omega_tilde is
+ * the indicator of the constraints Algorithm 3 ended with (of the initial
+ * constraints in the MSMFEM and EXPLICIT modes). */
+#define BDDC_CONSTRAINTS_ADAPTIVE 0
+#define BDDC_CONSTRAINTS_MSMFEM 1
+#define BDDC_CONSTRAINTS_EXPLICIT 2
+
 /* Coarse solver (Algorithm 1, the coarse problem of Step 1 and of every
  * preconditioner application).  Dense: the inverse of the coarse matrix,
  * applied as one dense matrix-vector product (per instance n_c^2 doubles).
@@ -117,6 +139,15 @@ typedef struct {
     const int32_t* partition; /* n_cells subdomain ids 0..N-1 (boxes or any
                                  face-connected sets) */
     const int8_t* bc_type;    /* n_faces, see above */
+    /* BDDC_CONSTRAINTS_EXPLICIT only (else 0 / NULL): n_rows constraint rows;
+       row r has the faces row_face[row_ptr[r] .. row_ptr[r + 1]) (face ids of
+       this instance) with the coefficients row_coef[same range].  All faces
+       of a row must be interface dofs of one face Gamma^{ij} between two
+       subdomains; otherwise the setup fails with BDDC_E_INVALID_ARG. */
+    int n_rows;
+    const int64_t* row_ptr;   /* n_rows + 1, row_ptr[0] = 0, non-decreasing */
+    const int64_t* row_face;
+    const double* row_coef;
 } bddc_instance;
 
 typedef struct {
@@ -132,6 +163,7 @@ typedef struct {
     int n_threads;        /* host threads used by setup; 0 = all cores */
     int coarse_solver;    /* BDDC_COARSE_* */
     int formulation;      /* BDDC_FORM_*; BDDC_FORM_FULL needs BDDC_PREC_FP64 */
+    int constraints;      /* BDDC_CONSTRAINTS_* */
 } bddc_options;
 
 typedef struct {
@@ -144,7 +176,8 @@ typedef struct {
     int n_subdomains;      /* N */
     int n_interface;       /* interface flux dofs (incl. pressure faces) */
     int n_coarse;          /* coarse dofs: flux constraints + N pressures */
-    int n_adaptive;        /* adaptive constraints added by Algorithm 3 */
+    int n_adaptive;        /* constraint rows added to the initial ones (Algorithm 3, MsMFEM or
+                              the caller's rows, per bddc_options.constraints) */
     double true_relres;    /* ||r|| / ||rhs|| of the full RT0/P0 saddle system (Sec. 2) at the
                               returned flux and pressure: both block rows, every free face and
                               cell, applied matrix-free on the GPU after the solve */
@@ -154,7 +187,7 @@ typedef struct bddc_handle bddc_handle;
 
 /* Default options: tau = 0 (face averages), multiplicity scaling, FP64,
  * maxit = 5000, pressure scaling on, all host threads, automatic coarse
- * solver, condensed operator. */
+ * solver, condensed operator, adaptive constraint mode. */
 void bddc_default_options(bddc_options* opt);
 
 /* Set up one or more independent instances (Algorithm 1 setup: local

@@ -38,6 +38,9 @@ BDDC_COARSE_SPARSE = 2
 BDDC_COARSE_DENSE_MAX = 2048
 BDDC_FORM_CONDENSED = 0
 BDDC_FORM_FULL = 1
+BDDC_CONSTRAINTS_ADAPTIVE = 0
+BDDC_CONSTRAINTS_MSMFEM = 1
+BDDC_CONSTRAINTS_EXPLICIT = 2
 
 
 class bddc_grid(C.Structure):
@@ -46,13 +49,14 @@ class bddc_grid(C.Structure):
 
 class bddc_instance(C.Structure):
     _fields_ = [("grid", bddc_grid), ("perm", C.c_void_p), ("perm_ncomp", C.c_int),
-                ("partition", C.c_void_p), ("bc_type", C.c_void_p)]
+                ("partition", C.c_void_p), ("bc_type", C.c_void_p), ("n_rows", C.c_int),
+                ("row_ptr", C.c_void_p), ("row_face", C.c_void_p), ("row_coef", C.c_void_p)]
 
 
 class bddc_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("scaling", C.c_int), ("precision", C.c_int),
                 ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int),
-                ("coarse_solver", C.c_int), ("formulation", C.c_int)]
+                ("coarse_solver", C.c_int), ("formulation", C.c_int), ("constraints", C.c_int)]
 
 
 class bddc_stats(C.Structure):
@@ -188,6 +192,19 @@ class _Keep:
             inst.perm_ncomp = 1 if perm.ndim == 1 else perm.shape[1]
             inst.partition = part.ctypes.data
             inst.bc_type = bct.ctypes.data
+            # caller constraint rows (BDDC_CONSTRAINTS_EXPLICIT): an optional
+            # attribute constraint_rows = [(face ids, coefficients), ...]
+            rows = getattr(pb, "constraint_rows", None) or []
+            if rows:
+                ptr = np.zeros(len(rows) + 1, dtype=np.int64)
+                ptr[1:] = np.cumsum([len(f) for f, _ in rows])
+                faces = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int64) for f, _ in rows]))
+                coef = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64) for _, c in rows]))
+                self.arrays += [ptr, faces, coef]
+                inst.n_rows = len(rows)
+                inst.row_ptr = ptr.ctypes.data
+                inst.row_face = faces.ctypes.data
+                inst.row_coef = coef.ctypes.data
 
 
 class Handle:

@@ -1793,6 +1793,7 @@ void bddc_default_options(bddc_options* opt) {
     opt->n_threads = 0;
     opt->coarse_solver = BDDC_COARSE_AUTO;
     opt->formulation = BDDC_FORM_CONDENSED;
+    opt->constraints = BDDC_CONSTRAINTS_ADAPTIVE;
 }
 
 const char* bddc_error_string(int code) {

@@ -60,6 +60,8 @@ struct Request {
     std::vector<double> perm, f, bc_value;
     std::vector<int32_t> part;
     std::vector<int8_t> bc_type;
+    std::vector<int64_t> row_ptr, row_face;  // caller constraint rows (BDDC_CONSTRAINTS_EXPLICIT)
+    std::vector<double> row_coef;
     double tol = 0.0;
     // result
     bool done = false;
@@ -76,6 +78,12 @@ struct Request {
         in.perm_ncomp = perm_ncomp;
         in.partition = part.data();
         in.bc_type = bc_type.data();
+        if (row_ptr.size() > 1) {
+            in.n_rows = (int)row_ptr.size() - 1;
+            in.row_ptr = row_ptr.data();
+            in.row_face = row_face.data();
+            in.row_coef = row_coef.data();
+        }
         return in;
     }
 };
@@ -282,6 +290,9 @@ void solve_batch(bddc_server* s, Batch& b) {
         std::vector<double>().swap(r->bc_value);
         std::vector<int32_t>().swap(r->part);
         std::vector<int8_t>().swap(r->bc_type);
+        std::vector<int64_t>().swap(r->row_ptr);
+        std::vector<int64_t>().swap(r->row_face);
+        std::vector<double>().swap(r->row_coef);
     }
     std::vector<double> flux((size_t)face_off[n]), pres((size_t)cell_off[n]);
     std::vector<int> its(n, 0);
@@ -385,6 +396,17 @@ int bddc_submit(bddc_server* s, const bddc_instance* inst, const double* f, cons
     r->perm.assign(inst->perm, inst->perm + nc * inst->perm_ncomp);
     r->part.assign(inst->partition, inst->partition + nc);
     r->bc_type.assign(inst->bc_type, inst->bc_type + nf);
+    if (inst->n_rows < 0) return BDDC_E_INVALID_ARG;
+    if (inst->n_rows > 0) {
+        if (!inst->row_ptr || !inst->row_face || !inst->row_coef) return BDDC_E_INVALID_ARG;
+        r->row_ptr.assign(inst->row_ptr, inst->row_ptr + inst->n_rows + 1);
+        const int64_t nnz = r->row_ptr.back();
+        if (r->row_ptr[0] != 0 || nnz < 0) return BDDC_E_INVALID_ARG;
+        for (int q = 0; q < inst->n_rows; ++q)
+            if (r->row_ptr[q + 1] < r->row_ptr[q]) return BDDC_E_INVALID_ARG;
+        r->row_face.assign(inst->row_face, inst->row_face + nnz);
+        r->row_coef.assign(inst->row_coef, inst->row_coef + nnz);
+    }
     r->f.assign(f, f + nc);
     r->bc_value.assign(bc_value, bc_value + nf);
     r->tol = tol;

@@ -127,6 +127,9 @@ struct Inst {
     std::vector<double> Kinv;       // (n_cf + N) square (dense coarse solver)
     CoarseFactor cf;                // multifrontal coarse factor (sparse coarse solver)
     double omega = 0.0;
+    // caller constraint rows (BDDC_CONSTRAINTS_EXPLICIT): CSR over face ids
+    std::vector<int64_t> xrow_ptr, xrow_face;
+    std::vector<double> xrow_coef;
 };
 
 template <class F>
@@ -204,6 +207,21 @@ SetupResult read_instance(const bddc_instance& in, Inst& I) {
         any_dir |= (t == 1);
     }
     I.pure = !any_dir;
+    if (in.n_rows < 0) return {BDDC_E_INVALID_ARG, "n_rows must be >= 0"};
+    if (in.n_rows > 0) {
+        if (!in.row_ptr || !in.row_face || !in.row_coef) return {BDDC_E_INVALID_ARG, "null constraint-row array"};
+        I.xrow_ptr.assign(in.row_ptr, in.row_ptr + in.n_rows + 1);
+        if (I.xrow_ptr[0] != 0) return {BDDC_E_INVALID_ARG, "row_ptr[0] must be 0"};
+        for (int r = 0; r < in.n_rows; ++r)
+            if (I.xrow_ptr[r + 1] < I.xrow_ptr[r]) return {BDDC_E_INVALID_ARG, "row_ptr must be non-decreasing"};
+        const int64_t nnz = I.xrow_ptr[in.n_rows];
+        I.xrow_face.assign(in.row_face, in.row_face + nnz);
+        I.xrow_coef.assign(in.row_coef, in.row_coef + nnz);
+        for (int64_t q = 0; q < nnz; ++q) {
+            if (I.xrow_face[q] < 0 || I.xrow_face[q] >= G.n_faces) return {BDDC_E_INVALID_ARG, "row face id out of range"};
+            if (!std::isfinite(I.xrow_coef[q])) return {BDDC_E_INVALID_ARG, "row coefficient not finite"};
+        }
+    }
     return res;
 }
 
@@ -1097,6 +1115,83 @@ SetupResult device_local_maps(std::vector<Inst>& I, const std::vector<std::pair<
     return {};
 }
 
+// The MsMFEM row of a face Gamma^{ij} (the comparison method of Sec. 5):
+// the face flux of the Darcy problem on Omega^i u Omega^j with the sources
+// 1/|Omega^i| and -1/|Omega^j| and no flow through the pair's boundary,
+// condensed onto the face.  With zero flux on the other interface dofs of
+// both subdomains, each subdomain's interface residual is S^k u_F + G_pre^k
+// w_k (its local maps); the two pressure constants enter the face rows as
+// a multiple of the net-flux row c, and mass balance fixes the net flux
+// through the face at int w_i = 1:
+//   [S_F  c] [u]   [-g_F]
+//   [c^T  0] [l] = [  1 ],   S_F = S^i_FF + S^j_FF, g_F = (G_pre^i w_i - G_pre^j w_j)_F.
+// Both subdomains' blocks are in global orientation, so S_F and g_F add.
+SetupResult msmfem_face(const Inst& I, const Face& F, std::vector<double>& row) {
+    const Sub& Si = I.subs[F.i];
+    const Sub& Sj = I.subs[F.j];
+    const int f = (int)F.gidx.size();
+    std::vector<int> pi(f), pj(f);
+    for (int q = 0; q < f; ++q) {
+        pi[q] = (int)(std::lower_bound(Si.gidx.begin(), Si.gidx.end(), F.gidx[q]) - Si.gidx.begin());
+        pj[q] = (int)(std::lower_bound(Sj.gidx.begin(), Sj.gidx.end(), F.gidx[q]) - Sj.gidx.begin());
+    }
+    const double wi = 1.0 / ((double)Si.nc * I.geo.vol), wj = 1.0 / ((double)Sj.nc * I.geo.vol);
+    const int n = f + 1;
+    std::vector<double> K((size_t)n * n, 0.0), rhs(n, 0.0);
+    for (int a = 0; a < f; ++a) {
+        for (int b = 0; b < f; ++b)
+            K[(size_t)a * n + b] = Si.S[(size_t)pi[a] * Si.ng + pi[b]] + Sj.S[(size_t)pj[a] * Sj.ng + pj[b]];
+        K[(size_t)a * n + f] = F.coef[a];
+        K[(size_t)f * n + a] = F.coef[a];
+        double g = 0.0;
+        for (int r = 0; r < Si.nc; ++r) g += Si.GpreT[(size_t)r * Si.ng + pi[a]] * wi;
+        for (int r = 0; r < Sj.nc; ++r) g -= Sj.GpreT[(size_t)r * Sj.ng + pj[a]] * wj;
+        rhs[a] = -g;
+    }
+    rhs[f] = 1.0;
+    std::vector<int> piv;
+    if (!lu(n, K.data(), piv)) return {BDDC_E_SETUP, "singular MsMFEM face problem"};
+    lu_solve(n, K.data(), piv, rhs.data(), 1);
+    row.assign(rhs.begin(), rhs.begin() + f);
+    return {};
+}
+
+// The caller's constraint rows of an instance, grouped by face: each row
+// over the dofs of one face Gamma^{ij} (in the face's dof order).
+SetupResult explicit_rows(const Inst& I, std::vector<std::vector<std::vector<double>>>& by_face) {
+    by_face.assign(I.faces.size(), {});
+    if (I.xrow_ptr.size() < 2) return {};
+    // interface index -> (face, position) for the faces between two subdomains
+    std::vector<int> gface(I.gamma.size(), -1), gpos(I.gamma.size(), -1);
+    for (int fi = 0; fi < (int)I.faces.size(); ++fi) {
+        const Face& F = I.faces[fi];
+        if (F.dir) continue;
+        for (int q = 0; q < (int)F.gidx.size(); ++q) {
+            gface[F.gidx[q]] = fi;
+            gpos[F.gidx[q]] = q;
+        }
+    }
+    for (size_t r = 0; r + 1 < I.xrow_ptr.size(); ++r) {
+        int fi = -1;
+        std::vector<double> row;
+        for (int64_t q = I.xrow_ptr[r]; q < I.xrow_ptr[r + 1]; ++q) {
+            const int64_t face = I.xrow_face[q];
+            const auto it = std::lower_bound(I.gamma.begin(), I.gamma.end(), face);
+            const int g = (it != I.gamma.end() && *it == face) ? (int)(it - I.gamma.begin()) : -1;
+            if (g < 0 || gface[g] < 0 || (fi >= 0 && gface[g] != fi))
+                return {BDDC_E_INVALID_ARG, "constraint row " + std::to_string(r) +
+                                                " is not on the dofs of one face between two subdomains"};
+            if (fi < 0) {
+                fi = gface[g];
+                row.assign(I.faces[fi].gidx.size(), 0.0);
+            }
+            row[gpos[g]] += I.xrow_coef[q];
+        }
+        if (fi >= 0) by_face[fi].push_back(row);
+    }
+    return {};
+}
+
 SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options& opt, Packed& P,
                       LocalMapsDevice device, FaceEigenDevice eig_device) {
     const int nthreads = opt.n_threads > 0 ? opt.n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
@@ -1138,7 +1233,8 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
     }
     stage.next("bddc_setup: weights and constraints (Algorithm 3)");
     for (int b = 0; b < n_inst; ++b) weights(I[b], opt.scaling);
-    const bool adaptive = opt.tau > 0 && std::isfinite(opt.tau);
+    const bool adaptive = opt.constraints == BDDC_CONSTRAINTS_ADAPTIVE && opt.tau > 0 && std::isfinite(opt.tau);
+    const bool add_rows = adaptive || opt.constraints != BDDC_CONSTRAINTS_ADAPTIVE;
     {
         std::vector<std::pair<int, int>> ftasks;
         for (int b = 0; b < n_inst; ++b)
@@ -1219,10 +1315,38 @@ SetupResult build_all(int n_inst, const bddc_instance* inst, const bddc_options&
                 om[t] = adaptive_face(I[b], I[b].faces[fi], adaptive ? opt.tau : -1.0, rows[t]);
             });
         }
+        // the other constraint modes: MsMFEM rows or the caller's rows
+        // (Algorithm 3 above still gives omega-tilde of the initial constraints)
+        if (opt.constraints == BDDC_CONSTRAINTS_MSMFEM) {
+            std::vector<SetupResult> fres(ftasks.size());
+            parallel_for((int64_t)ftasks.size(), nthreads, [&](int64_t t) {
+                auto [b, fi] = ftasks[t];
+                std::vector<double> row;
+                fres[t] = msmfem_face(I[b], I[b].faces[fi], row);
+                rows[t] = fres[t].code ? std::vector<std::vector<double>>{}
+                                       : orthonormalize(I[b].faces[fi].rows, {row});
+            });
+            for (auto& r : fres)
+                if (r.code) return r;
+        } else if (opt.constraints == BDDC_CONSTRAINTS_EXPLICIT) {
+            std::vector<std::vector<std::vector<std::vector<double>>>> xr(n_inst);
+            for (int b = 0; b < n_inst; ++b) {
+                SetupResult r = explicit_rows(I[b], xr[b]);
+                if (r.code) {
+                    r.msg = "instance " + std::to_string(b) + ": " + r.msg;
+                    return r;
+                }
+            }
+            parallel_for((int64_t)ftasks.size(), nthreads, [&](int64_t t) {
+                auto [b, fi] = ftasks[t];
+                rows[t] = xr[b][fi].empty() ? std::vector<std::vector<double>>{}
+                                            : orthonormalize(I[b].faces[fi].rows, xr[b][fi]);
+            });
+        }
         for (size_t t = 0; t < ftasks.size(); ++t) {
             auto [b, fi] = ftasks[t];
             I[b].omega = std::max(I[b].omega, om[t]);
-            if (!adaptive) continue;
+            if (!add_rows) continue;
             Face& F = I[b].faces[fi];
             for (auto& r : rows[t]) {
                 F.rows.push_back(r);

@@ -372,3 +372,54 @@ def test_edge_cases(bddc):
     with pytest.raises(bddc.BDDCError) as e:
         bddc.setup([bad])
     assert e.value.code == bddc.BDDC_E_PERM
+
+
+@pytest.mark.parametrize("case", ["c1", "irregular3d_anisotropic", "tiny3d"])
+def test_msmfem_and_explicit_constraints_match_oracle(bddc, case):
+    """The comparison constraints of Sec. 5 (BDDC_CONSTRAINTS_MSMFEM) and
+    caller-given rows (BDDC_CONSTRAINTS_EXPLICIT) on the GPU: FP64 against
+    the oracle at tol 1e-8 (iterations, kappa, solution) and 1e-12, the
+    mixed path within its bound; the explicit rows also through the serving
+    loop, bitwise equal to the solo solve (source-free fields: the library's
+    setup distributes the pair sources uniformly)."""
+    pb = CASES[case]()
+    pb.f = np.zeros(pb.grid.n_cells)
+    o = BDDCOracle(pb, constraints="msmfem")
+    ref = o.solve(tol=1e-8)
+    M = bddc.BDDC_CONSTRAINTS_MSMFEM
+
+    def solve(pbx, tol, prec, mode):
+        opt = bddc.default_options(precision=prec, constraints=mode)
+        h = bddc.setup([pbx], opt, stream=torch.cuda.current_stream().cuda_stream)
+        flux, pres = np.empty(len(pbx.bc_value)), np.empty(pbx.grid.n_cells)
+        its = np.zeros(1, dtype=np.int32)
+        h.solve(pbx.f, pbx.bc_value, tol, flux, pres, its)
+        st = h.stats(0)
+        h.close()
+        return flux, pres, int(its[0]), st
+
+    flux, pres, its, st = solve(pb, 1e-8, bddc.BDDC_PREC_FP64, M)
+    assert st.n_coarse == o.n_coarse
+    assert abs(its - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert abs(st.kappa - ref.kappa) <= 0.02 * ref.kappa
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    f32, p32, _, _ = solve(pb, 1e-8, bddc.BDDC_PREC_FP32, M)
+    assert _rel(f32, ref.flux) <= MIXED_REL and _rel(p32, ref.pressure) <= MIXED_REL
+    ref12 = o.solve(tol=1e-12)
+    f12, p12, _, _ = solve(pb, 1e-12, bddc.BDDC_PREC_FP64, M)
+    bound = converged_bound(o, ref12)
+    assert _rel(f12, ref12.flux) <= bound and _rel(p12, ref12.pressure) <= bound
+    # explicit rows: the oracle's MsMFEM rows handed in by the caller
+    pb.constraint_rows = [(fa["dofs"], fa["rows"][1]) for fa in o.ss.faces if fa["kind"] == "F"]
+    X = bddc.BDDC_CONSTRAINTS_EXPLICIT
+    fx, px, itx, stx = solve(pb, 1e-8, bddc.BDDC_PREC_FP64, X)
+    assert stx.n_coarse == o.n_coarse
+    assert _rel(fx, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    srv = bddc.Server(bddc.default_options(constraints=X), hbm_budget_bytes=4 << 30, max_batch=4)
+    t = srv.submit(pb, tol=1e-8)
+    srv.wait(t)
+    rc, fs, ps, its_s, _, _ = srv.poll(t)
+    srv.close()
+    assert rc == bddc.BDDC_OK and its_s == itx
+    assert np.array_equal(fs, fx) and np.array_equal(ps, px)

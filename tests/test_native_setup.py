@@ -276,3 +276,57 @@ def test_stiffness_scaling_setup_matches_oracle(case, tau):
     if tau is not None:
         assert np.isclose(hs.get("inst_omega")[0], o.omega_tilde, rtol=1e-8)
         assert int(hs.get("inst_ncn")[0]) == o.n_coarse
+
+
+def _source_free(pb):
+    pb.f = np.zeros(pb.grid.n_cells)
+    return pb
+
+
+@pytest.mark.parametrize("case", ["c1", "irregular2d", "tiny3d"])
+def test_msmfem_constraints_setup_matches_oracle(case):
+    """BDDC_CONSTRAINTS_MSMFEM (Sec. 5): the native rows come from the pair
+    problem condensed onto the face with the local maps (bordered by the
+    net-flux row), the oracle's from the pair's full Darcy problem; both
+    give the same coarse space and solve (source-free fields: the library's
+    setup uses the uniform source distribution)."""
+    pb = _source_free(CASES[case]())
+    hs = bddc.HostSetup([pb], bddc.default_options(constraints=bddc.BDDC_CONSTRAINTS_MSMFEM))
+    P = Packed(hs)
+    o = BDDCOracle(pb, constraints="msmfem")
+    assert int(hs.get("inst_ncn")[0]) == o.n_coarse
+    _, _, its, al, be = emulate_solve(P, pb.f, pb.bc_value, 1e-8)
+    r = o.solve(tol=1e-8)
+    assert abs(int(its[0]) - r.iterations) <= iteration_slack(r.iterations, r.kappa)
+    assert abs(lanczos_condition(al[0], be[0]) - r.kappa) <= 1e-2 * r.kappa
+    flux, pres, _, _, _ = emulate_solve(P, pb.f, pb.bc_value, 1e-12)
+    r = o.solve(tol=1e-12)
+    assert np.linalg.norm(flux - r.flux) <= 1e-9 * np.linalg.norm(r.flux)
+    assert np.linalg.norm(pres - r.pressure) <= 1e-8 * np.linalg.norm(r.pressure)
+
+
+def test_explicit_constraint_rows_setup_matches_oracle_and_rejects_bad_rows():
+    """BDDC_CONSTRAINTS_EXPLICIT: caller rows (the oracle's MsMFEM rows and
+    a random row on some faces) give the oracle's coarse space and solve; a
+    row over the dofs of two faces is rejected with BDDC_E_INVALID_ARG."""
+    pb = make_config("c1")
+    ms = BDDCOracle(pb, constraints="msmfem")
+    rng = np.random.default_rng(12)
+    rows = []
+    for k, face in enumerate(f for f in ms.ss.faces if f["kind"] == "F"):
+        rows.append((face["dofs"], face["rows"][1]))
+        if k % 3 == 0:
+            rows.append((face["dofs"], rng.standard_normal(len(face["dofs"]))))
+    pb.constraint_rows = rows
+    hs = bddc.HostSetup([pb], bddc.default_options(constraints=bddc.BDDC_CONSTRAINTS_EXPLICIT))
+    o = BDDCOracle(pb, constraints="explicit", explicit_rows=rows)
+    assert int(hs.get("inst_ncn")[0]) == o.n_coarse
+    flux, pres, _, _, _ = emulate_solve(Packed(hs), pb.f, pb.bc_value, 1e-12)
+    r = o.solve(tol=1e-12)
+    assert np.linalg.norm(flux - r.flux) <= 1e-9 * np.linalg.norm(r.flux)
+    assert np.linalg.norm(pres - r.pressure) <= 1e-8 * np.linalg.norm(r.pressure)
+    f0, f1 = [f for f in ms.ss.faces if f["kind"] == "F"][:2]
+    pb.constraint_rows = [(np.concatenate([f0["dofs"][:1], f1["dofs"][:1]]), np.ones(2))]
+    with pytest.raises(bddc.BDDCError) as e:
+        bddc.HostSetup([pb], bddc.default_options(constraints=bddc.BDDC_CONSTRAINTS_EXPLICIT))
+    assert e.value.code == bddc.BDDC_E_INVALID_ARG
