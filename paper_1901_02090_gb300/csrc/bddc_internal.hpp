@@ -98,6 +98,10 @@ struct Packed {
     int max_ng = 0, max_m = 0, max_ncn = 0, max_out_post = 0, max_in_post = 0;
 };
 
+// steps of iterative refinement of the dense local maps (host and device
+// alike, so that both compute the same maps)
+constexpr int kLocalRefinements = 1;
+
 // the option values every entry point accepts
 inline bool options_valid(const bddc_options& o) {
     return o.maxit > 0 && (o.precision == BDDC_PREC_FP64 || o.precision == BDDC_PREC_FP32) &&

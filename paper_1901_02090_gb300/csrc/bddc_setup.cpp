@@ -500,9 +500,12 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
     std::vector<int> piv;
     if (!lu(nq, Qm.data(), piv)) return {BDDC_E_SETUP, "singular local pressure Schur complement"};
 
-    // solve for the ng + nc input columns, with two steps of iterative
+    // solve for the ng + nc input columns, with one step of iterative
     // refinement against the exact sparse local operator (the elimination
-    // loses accuracy in proportion to the permeability contrast)
+    // loses accuracy in proportion to the permeability contrast).  One step
+    // suffices: on the 1e7-contrast 60x220 fields a second step changes S^i
+    // by 2e-16 and G_post by 6e-12 relative, and the solution's distance to
+    // the direct solve of the assembled system not at all.
     const int ncol = ng + nc;
     std::vector<double> XU((size_t)ncol * ni, 0.0);    // interior rhs per column
     std::vector<double> XP((size_t)nq * ncol, 0.0);    // pressure/mu rhs, nq x ncol
@@ -542,7 +545,7 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
     solve_all(XU, XP, YU, YPM);
     {
         std::vector<double> RU((size_t)ncol * ni), RP((size_t)nq * ncol), DU, DPM;
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < kLocalRefinements; ++pass) {
             // residual of K_I y against the right-hand side
             for (int j = 0; j < ncol; ++j) {
                 const double* yu = &YU[(size_t)j * ni];

@@ -9,11 +9,12 @@
 // host); eliminating it leaves the dense pressure Schur complement
 //     Q = [[-dB_I A_II^{-1} dB_I^T, v], [v^T, 0]]      (n_c + 1 square)
 // which is LU-factored with partial pivoting.  All right-hand sides are
-// solved together and refined twice against the exact sparse local
+// solved together and refined against the exact sparse local
 // operator (the elimination loses accuracy in proportion to the
 // permeability contrast).  This is the algorithm of local_maps in
-// bddc_setup.cpp step by step; here one CTA takes one subdomain and its
-// threads take the right-hand-side columns, in FP64.
+// bddc_setup.cpp step by step (kLocalRefinements steps of refinement);
+// here one CTA takes one subdomain and its threads take the
+// right-hand-side columns, in FP64.
 //
 // Scratch layouts are column-fastest ([row * ncol + column]) so that the
 // threads of a warp, one column each, touch consecutive addresses.
@@ -511,7 +512,7 @@ int local_maps_device(LocalMapsBatch& B, std::string& err) {
             k_lm_rhs<<<cnt, kLmThreads, 0, st>>>(v);
             k_lm_solve<<<cnt, kLmThreads, 0, st>>>(v, v.XU, v.XP, v.YU, v.YP);
             const int64_t nU = all[2 * k + cnt], nP = all[3 * k + cnt];
-            for (int pass = 0; pass < 2; ++pass) {
+            for (int pass = 0; pass < kLocalRefinements; ++pass) {
                 k_lm_resid<<<cnt, kLmThreads, 0, st>>>(v);
                 k_lm_solve<<<cnt, kLmThreads, 0, st>>>(v, v.RU, v.RP, v.DU, v.DP);
                 k_lm_add<<<(int)std::min<int64_t>((nU + 255) / 256, 65536), 256, 0, st>>>(nU, v.YU, v.DU);
