@@ -57,6 +57,8 @@ def parse():
                     help="60x220x85 configurations timed beside the headline (comma-separated; '' for none)")
     ap.add_argument("--large-steps", type=int, default=5, help="timed solves of each large configuration")
     ap.add_argument("--no-fp64-batch", action="store_true", help="skip the batched FP64 line")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1: the setups pick the solve launch's work layout by probe launches")
     return ap.parse_args()
 
 
@@ -351,6 +353,14 @@ def serving_run(args, rank, rate):
             "iterations_mean": float(np.mean(its)), "device_bytes_peak": int(peak)}
 
 
+def _tuning(h):
+    """The solve launch's work layout and the probe times that chose it."""
+    t = h.tuning()
+    return {"tuned": bool(t.tuned), "from_cache": bool(t.from_cache), "balance_weight": t.balance_weight,
+            "coarse_rows": t.coarse_rows, "probe_ms": round(t.probe_ms, 4),
+            "probe_ms_heuristic": round(t.probe_ms_default, 4)}
+
+
 def large_config(args, name, dev, stream, peak):
     """One 60x220x85 field (c3: 12x44x17 boxes of 5^3; c4: seeded boxes of
     3-8 cells per axis), tau = 10, mixed path, the sparse coarse solver
@@ -362,9 +372,10 @@ def large_config(args, name, dev, stream, peak):
     from synth import make_config
     pb = make_config(name)
     t0 = time.perf_counter()
-    h = bddc.setup([pb], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32),
+    h = bddc.setup([pb], bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32, autotune=args.autotune),
                    stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
+    tuning = _tuning(h)
     f = torch.as_tensor(pb.f, device=dev)
     bc = torch.as_tensor(pb.bc_value, device=dev)
     flux = torch.empty(len(pb.bc_value), dtype=torch.float64, device=dev)
@@ -391,7 +402,7 @@ def large_config(args, name, dev, stream, peak):
                         f", tau={args.tau:g}, mixed path, sparse coarse solver",
             "ms_per_solve": wall, "kernel_ms": km, "solves_per_s": 1e3 / wall,
             "iterations": st.iterations, "n_subdomains": st.n_subdomains, "n_coarse": st.n_coarse,
-            "true_relres": st.true_relres, "setup_s": round(setup_s, 2),
+            "true_relres": st.true_relres, "setup_s": round(setup_s, 2), "tuning": tuning,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes_per_launch": by}}
 
@@ -402,7 +413,9 @@ def batched_fp64(args, pbs, dev, stream, peak, K):
     batching gain."""
     import torch
     from paper_1901_02090_gb300 import bddc
-    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64), stream=stream.cuda_stream)
+    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP64, autotune=args.autotune),
+                   stream=stream.cuda_stream)
+    tuning = _tuning(h)
     f = torch.as_tensor(np.concatenate([pb.f for pb in pbs]), device=dev)
     bc = torch.as_tensor(np.concatenate([pb.bc_value for pb in pbs]), device=dev)
     flux = torch.empty(len(bc), dtype=torch.float64, device=dev)
@@ -428,7 +441,7 @@ def batched_fp64(args, pbs, dev, stream, peak, K):
     ach = by / (km / 1e3) / 1e9
     return {"value": len(pbs) * K / (total / 1e3), "unit": "solves/s", "batch": len(pbs), "steps": K,
             "ms_per_step": total / K, "kernel_ms": km, "iterations_mean": float(np.mean(its)),
-            "true_relres_max": tr,
+            "true_relres_max": tr, "tuning": tuning,
             "roofline": {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                          "algorithmic_bytes_per_launch": by}}
 
@@ -507,8 +520,10 @@ def main():
     # ---- batched mixed-precision path -----------------------------------------
     pbs = problems(rank, B)
     t0 = time.perf_counter()
-    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32), stream=sptr)
+    h = bddc.setup(pbs, bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32, autotune=args.autotune),
+                   stream=sptr)
     setup_s = time.perf_counter() - t0
+    tuning = _tuning(h)
     f_h = np.ascontiguousarray(np.concatenate([pb.f for pb in pbs]))
     bc_h = np.ascontiguousarray(np.concatenate([pb.bc_value for pb in pbs]))
     f_d = torch.as_tensor(f_h, device=dev)
@@ -603,7 +618,7 @@ def main():
         "config": {"workload": WORKLOAD, "batch": B, "tau": args.tau, "tol": args.tol,
                    "grid": "60x220 cells, 20x10 ft", "subdomains": "6x22 of 10x10",
                    "l2": "operators streamed per iteration exceed L2 (inputs larger than L2)",
-                   "setup_s": round(setup_s, 2)},
+                   "setup_s": round(setup_s, 2), "tuning": tuning},
         "iterations": {"mean": float(np.mean(iters)), "min": int(min(iters)), "max": int(max(iters))},
         "kappa_mean": float(np.mean(kappas)), "adaptive_constraints_mean": float(np.mean(n_adapt)),
         # ||r|| / ||rhs|| of the full RT0/P0 system at each returned solution (GPU, after the solve)

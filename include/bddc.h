@@ -164,6 +164,8 @@ typedef struct {
     int coarse_solver;    /* BDDC_COARSE_* */
     int formulation;      /* BDDC_FORM_*; BDDC_FORM_FULL needs BDDC_PREC_FP64 */
     int constraints;      /* BDDC_CONSTRAINTS_* */
+    int autotune;         /* 1: pick the launch's work layout by timing short probe solves at
+                             setup (see bddc_get_tuning); 0: the fixed heuristic */
 } bddc_options;
 
 typedef struct {
@@ -289,6 +291,32 @@ int bddc_subassembled_apply_noalloc(int n_sub, const int* ng, const int64_t* slo
                                     const int64_t* S_offset, const double* S, const int* gidx,
                                     const int* partner, int64_t n_interface, const double* u,
                                     double* q, void* stream);
+
+/* Work layout of the persistent solve kernel and how it was chosen.  Each
+ * warp takes a contiguous range of subdomains of equal summed cost
+ * n_Gamma^2 + balance_weight (the operator blocks plus a fixed latency per
+ * subdomain); each CTA takes units of coarse_rows rows of the dense coarse
+ * inverse.  With bddc_options.autotune the setup times the persistent kernel
+ * itself on the handle's operators (six CG iterations on a constant
+ * right-hand side, the minimum of two launches) for the weights 0, 1024,
+ * 4096, 16384 and 65536 and then, for the dense coarse solver, the unit
+ * sizes 8, 16 and 32 rows (those that leave the launch grid unchanged), and
+ * keeps the fastest, the heuristic winning ties within 1 %.  The choice is
+ * cached per signature (launch grid, batch size, interface and constraint
+ * sizes of every subdomain, coarse sizes, precision, form) for later setups
+ * of the process.  A probe that fails to launch or times out leaves the
+ * heuristic in place.  Without autotune: 4096 and 16.  Tuning allocates the
+ * host-array staging buffers of bddc_solve at setup.  Returns BDDC_OK, or
+ * BDDC_E_INVALID_ARG for a null argument. */
+typedef struct {
+    int tuned;                /* 1: chosen by probe solves (or taken from the cache), 0: heuristic */
+    int from_cache;           /* 1: the choice of an earlier setup with the same signature */
+    double balance_weight;    /* C of the warp ranges */
+    int coarse_rows;          /* rows of a dense-coarse work unit */
+    double probe_ms;          /* the chosen layout's probe time (0 if not tuned) */
+    double probe_ms_default;  /* the heuristic layout's probe time (0 if not tuned) */
+} bddc_tuning;
+int bddc_get_tuning(const bddc_handle* h, bddc_tuning* out);
 
 /* Device time (ms) of the last solve's main kernel (the persistent Step 1-3
  * kernel), measured with CUDA events around its launch, and the algorithmic

@@ -56,7 +56,13 @@ class bddc_instance(C.Structure):
 class bddc_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("scaling", C.c_int), ("precision", C.c_int),
                 ("maxit", C.c_int), ("pressure_scaling", C.c_int), ("n_threads", C.c_int),
-                ("coarse_solver", C.c_int), ("formulation", C.c_int), ("constraints", C.c_int)]
+                ("coarse_solver", C.c_int), ("formulation", C.c_int), ("constraints", C.c_int),
+                ("autotune", C.c_int)]
+
+
+class bddc_tuning(C.Structure):
+    _fields_ = [("tuned", C.c_int), ("from_cache", C.c_int), ("balance_weight", C.c_double),
+                ("coarse_rows", C.c_int), ("probe_ms", C.c_double), ("probe_ms_default", C.c_double)]
 
 
 class bddc_stats(C.Structure):
@@ -96,6 +102,7 @@ def _load():
         "bddc_solve": (C.c_int, [P, P, P, C.c_double, P, P, P]),
         "bddc_get_stats": (C.c_int, [P, C.c_int, P]),
         "bddc_sizes": (C.c_int, [P, P, P, P]),
+        "bddc_get_tuning": (C.c_int, [P, P]),
         "bddc_apply_operator": (C.c_int, [P, P, P, P]),
         "bddc_apply_preconditioner": (C.c_int, [P, P, P, P]),
         "bddc_subassembled_apply": (C.c_int, [C.c_int, P, P, P, P, P, P, C.c_int64, P, P, P, P]),
@@ -128,7 +135,7 @@ def _load():
 
 
 lib = _load()
-EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes",
+EXPORTED = ("bddc_default_options", "bddc_setup", "bddc_solve", "bddc_get_stats", "bddc_sizes", "bddc_get_tuning",
             "bddc_apply_operator", "bddc_apply_preconditioner", "bddc_subassembled_apply",
             "bddc_subassembled_apply_noalloc",
             "bddc_last_solve_timing", "bddc_host_setup_create", "bddc_host_setup_create_gpu", "bddc_host_setup_query",
@@ -243,6 +250,13 @@ class Handle:
         if rc != BDDC_OK:
             raise BDDCError(rc)
         return st
+
+    def tuning(self) -> bddc_tuning:
+        t = bddc_tuning()
+        rc = lib.bddc_get_tuning(self._h, C.byref(t))
+        if rc != BDDC_OK:
+            raise BDDCError(rc)
+        return t
 
     def sizes(self):
         ni, ng, ns = C.c_int(), C.c_int64(), C.c_int64()

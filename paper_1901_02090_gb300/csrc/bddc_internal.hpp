@@ -106,7 +106,7 @@ constexpr int kLocalRefinements = 1;
 inline bool options_valid(const bddc_options& o) {
     return o.maxit > 0 && (o.precision == BDDC_PREC_FP64 || o.precision == BDDC_PREC_FP32) &&
            (o.scaling == BDDC_SCALING_MULTIPLICITY || o.scaling == BDDC_SCALING_STIFFNESS) &&
-           o.coarse_solver >= BDDC_COARSE_AUTO && o.coarse_solver <= BDDC_COARSE_SPARSE &&
+           o.coarse_solver >= BDDC_COARSE_AUTO && o.coarse_solver <= BDDC_COARSE_SPARSE && (o.autotune == 0 || o.autotune == 1) &&
            o.constraints >= BDDC_CONSTRAINTS_ADAPTIVE && o.constraints <= BDDC_CONSTRAINTS_EXPLICIT &&
            (o.formulation == BDDC_FORM_CONDENSED ||
             (o.formulation == BDDC_FORM_FULL && o.precision == BDDC_PREC_FP64));

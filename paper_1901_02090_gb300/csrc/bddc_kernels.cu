@@ -634,7 +634,7 @@ __device__ void ph_coarse(const Params& p, int64_t u, bool step1, double* rhs, i
     const uint64_t pol = l2_stream_policy();
     const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t r0 = p.cunit_row0[u];
-    const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
+    const int64_t r1 = (r0 + p.coarse_rows < ncn) ? r0 + p.coarse_rows : ncn;
     for (int64_t row = r0 + wi; row < r1; row += kWarps) {
         const K_t* kr = K + row * ncn;
         double acc;
@@ -1705,6 +1705,7 @@ struct bddc_handle {
     int64_t* d_cfoff = nullptr;
     double bytes_iter = 0.0, bytes_pre = 0.0, bytes_post = 0.0;
     mutable std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
+    bddc_tuning tuning{};                        // work layout of the solve launch
 };
 
 // message of the last failed setup of this thread (bddc_last_error(NULL));
@@ -1794,6 +1795,7 @@ void bddc_default_options(bddc_options* opt) {
     opt->coarse_solver = BDDC_COARSE_AUTO;
     opt->formulation = BDDC_FORM_CONDENSED;
     opt->constraints = BDDC_CONSTRAINTS_ADAPTIVE;
+    opt->autotune = 0;
 }
 
 const char* bddc_error_string(int code) {
@@ -1857,6 +1859,203 @@ const void* solve_kernel_fn(int precision, int formulation, bool bal) {
     return bal ? (const void*)bddc_solve_kernel<PrecFP64, true> : (const void*)bddc_solve_kernel<PrecFP64, false>;
 }
 
+// dense-coarse work units of `rows` rows each: instance, first row, and the
+// first unit of every instance (n_inst + 1 entries)
+void coarse_units(const Packed& P, int n_inst, int rows, std::vector<int>& cu_inst, std::vector<int>& cu_row0,
+                  std::vector<int64_t>& cu0) {
+    cu_inst.clear();
+    cu_row0.clear();
+    cu0.assign(1, 0);
+    for (int b = 0; b < n_inst; ++b) {
+        for (int64_t r0 = 0; r0 < P.inst_ncn[b]; r0 += rows) {
+            cu_inst.push_back(b);
+            cu_row0.push_back((int)r0);
+        }
+        cu0.push_back((int64_t)cu_inst.size());
+    }
+}
+
+// contiguous subdomain ranges of W warps at equal fractions of the summed
+// cost n_Gamma^2 + C: the operators S and F (n_Gamma^2) plus a fixed latency
+// cost of a subdomain (gathers, reductions, arrivals); W + 1 entries
+std::vector<int64_t> warp_ranges(const Packed& P, int64_t NS, int64_t W, double C) {
+    std::vector<double> pre(NS + 1, 0.0);
+    for (int64_t s = 0; s < NS; ++s) pre[s + 1] = pre[s] + (double)P.sub_ng[s] * P.sub_ng[s] + C;
+    std::vector<int64_t> ws(W + 1);
+    int64_t s = 0;
+    for (int64_t w = 0; w < W; ++w) {
+        const double target = pre[NS] * (double)w / (double)W;
+        while (s < NS && pre[s] < target) ++s;
+        ws[w] = s;
+    }
+    ws[W] = NS;
+    return ws;
+}
+
+// launch grid of the persistent kernel: one CTA per subdomain or coarse unit,
+// at most the resident CTAs of the device
+int solve_grid(int nb, int nsm, int64_t n_sub, int64_t n_cunits) {
+    const int64_t want = std::max<int64_t>(n_sub, n_cunits);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb * nsm, want));
+}
+
+constexpr double kBalanceWeight = 4096.0;  // C of the heuristic warp ranges
+constexpr int kProbeIters = 6;             // CG iterations of a tuning probe
+
+// the layouts chosen by earlier tuned setups of this process, by signature
+std::mutex g_tune_mu;
+std::vector<std::pair<uint64_t, bddc_tuning>> g_tune_cache;
+
+// FNV-1a over what decides the kernel's time per iteration: the launch, the
+// subdomains' interface and constraint sizes, the coarse problem
+uint64_t tune_signature(const bddc_handle* h, int grid) {
+    uint64_t x = 1469598103934665603ULL;
+    auto mix = [&](int64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            x ^= (uint64_t)((v >> (8 * i)) & 0xff);
+            x *= 1099511628211ULL;
+        }
+    };
+    const Packed& P = h->P;
+    mix(h->precision);
+    mix(h->formulation);
+    mix(h->n_inst);
+    mix(grid);
+    mix(P.coarse_sparse ? 1 : 0);
+    mix((int64_t)P.sub_ng.size());
+    for (size_t s = 0; s < P.sub_ng.size(); ++s) {
+        mix(P.sub_ng[s]);
+        mix(P.sub_m[s]);
+    }
+    for (int b = 0; b < h->n_inst; ++b) mix(P.inst_ncn[b]);
+    mix((int64_t)P.cn_p.size());
+    return x;
+}
+
+// device time (ms) of one probe launch of the persistent kernel with the
+// layout in p: kProbeIters CG iterations (tolerance 0) on the handle's
+// constant probe data; -1 on a launch error or a barrier timeout
+float probe_launch(bddc_handle* h, Params p) {
+    cudaStream_t st = h->stream;
+    p.maxit = std::min(kProbeIters, p.maxit);  // the CG history's pitch stays within the handle's
+    p.tol = 0.0;
+    p.f_in = h->d_f;
+    p.bc_in = h->d_bc;
+    p.flux_out = h->d_flux;
+    p.p_out = h->d_p;
+    cudaMemsetAsync(p.flux_out, 0, (size_t)h->total_faces * sizeof(double), st);
+    cudaMemsetAsync(p.st, 0, sizeof(InstState) * h->n_inst, st);
+    cudaMemsetAsync(p.inst_cnt, 0, sizeof(int) * kCounters * (size_t)h->n_inst, st);
+    cudaMemsetAsync(p.gsync, 0, sizeof(GridSync), st);
+    cudaMemsetAsync(p.tstamp, 0, 2 * sizeof(long long) * (size_t)p.tstamp_cap, st);
+    cudaMemcpyAsync(p.n_active, &h->n_inst, sizeof(int), cudaMemcpyHostToDevice, st);
+    void* args[] = {&p};
+    const void* kfn = solve_kernel_fn(h->precision, h->formulation, p.act_n > 1);
+    cudaEventRecord(h->ev0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(h->grid), dim3(kThreads), args, h->smem, st);
+    cudaEventRecord(h->ev1, st);
+    if (e != cudaSuccess) return -1.0f;
+    cudaMemcpyAsync(h->pin_gs, p.gsync, sizeof(GridSync), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || h->pin_gs->error) return -1.0f;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    return ms;
+}
+
+// Autotuning of the work layout (bddc_options.autotune): time probe launches
+// of the persistent kernel for the warp-range weights C and, with the dense
+// coarse solver, the unit sizes; keep the fastest (the heuristic wins ties
+// within 1 %).  ws_dev is the warp-range buffer (grid * kWarps + 1 entries),
+// cu_* the unit buffers, sized for the smallest unit.  Returns BDDC_OK or a
+// CUDA error; the handle keeps the heuristic layout when a probe fails.
+int autotune_layout(bddc_handle* h, int64_t* ws_dev, int* cu_inst_dev, int* cu_row0_dev, int64_t* cu0_dev, int nb,
+                    int nsm) {
+    const Packed& P = h->P;
+    Params& p = h->prm;
+    const int64_t NS = P.n_sub, W = (int64_t)h->grid * kWarps;
+    const uint64_t sig = tune_signature(h, h->grid);
+    bddc_tuning& T = h->tuning;
+    std::vector<int> ci, cr;
+    std::vector<int64_t> c0;
+    auto set_rows = [&](int rows) -> bool {
+        coarse_units(P, h->n_inst, rows, ci, cr, c0);
+        if (!ci.empty() && (cudaMemcpy(cu_inst_dev, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+                            cudaMemcpy(cu_row0_dev, cr.data(), cr.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+            return false;
+        if (cudaMemcpy(cu0_dev, c0.data(), c0.size() * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+        p.n_cunits = (int64_t)ci.size();
+        p.coarse_rows = rows;
+        return true;
+    };
+    auto set_weight = [&](double C) -> bool {
+        const std::vector<int64_t> ws = warp_ranges(P, NS, W, C);
+        return cudaMemcpy(ws_dev, ws.data(), ws.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto& e : g_tune_cache)
+            if (e.first == sig) {
+                T = e.second;
+                T.from_cache = 1;
+                break;
+            }
+    }
+    if (T.from_cache) {
+        if (!set_weight(T.balance_weight) || !set_rows(T.coarse_rows)) return BDDC_E_CUDA;
+        return BDDC_OK;
+    }
+    cudaMemset(h->d_f, 0x3f, (size_t)h->total_cells * sizeof(double));  // a constant 4.8e-4 in every cell
+    cudaMemset(h->d_bc, 0, (size_t)h->total_faces * sizeof(double));
+    if (cudaDeviceSynchronize() != cudaSuccess) return BDDC_E_CUDA;
+    auto time_layout = [&]() -> float {
+        float best = -1.0f;
+        for (int r = 0; r < 2; ++r) {
+            const float ms = probe_launch(h, p);
+            if (ms < 0.0f) return -1.0f;
+            best = best < 0.0f ? ms : std::min(best, ms);
+        }
+        return best;
+    };
+    if (probe_launch(h, p) < 0.0f) return BDDC_OK;  // warm-up; on failure keep the heuristic
+    const float t_def = time_layout();
+    if (t_def < 0.0f) return BDDC_OK;
+    double bestC = kBalanceWeight;
+    int best_rows = p.coarse_rows;
+    float best_t = t_def;
+    for (double C : {0.0, 1024.0, 16384.0, 65536.0}) {
+        if (!set_weight(C)) return BDDC_E_CUDA;
+        const float t = time_layout();
+        if (t >= 0.0f && t < 0.99f * best_t) {
+            best_t = t;
+            bestC = C;
+        }
+    }
+    if (!set_weight(bestC)) return BDDC_E_CUDA;
+    if (!P.coarse_sparse) {
+        for (int rows : {8, 32}) {
+            std::vector<int> a, b;
+            std::vector<int64_t> c;
+            coarse_units(P, h->n_inst, rows, a, b, c);
+            if (solve_grid(nb, nsm, NS, (int64_t)a.size()) != h->grid) continue;  // the warp ranges would change
+            if (!set_rows(rows)) return BDDC_E_CUDA;
+            const float t = time_layout();
+            if (t >= 0.0f && t < 0.99f * best_t) {
+                best_t = t;
+                best_rows = rows;
+            }
+        }
+        if (!set_rows(best_rows)) return BDDC_E_CUDA;
+    }
+    T.tuned = 1;
+    T.balance_weight = bestC;
+    T.coarse_rows = best_rows;
+    T.probe_ms = best_t;
+    T.probe_ms_default = t_def;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.emplace_back(sig, T);
+    return BDDC_OK;
+}
+
 // device part of bddc_setup: upload a batch's host setup and size the launch
 int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_stream, Packed&& packed,
                       bddc_handle** out) {
@@ -1874,16 +2073,10 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         h->total_cells += P.inst_ncells[b];
         h->total_faces += P.inst_nfaces[b];
     }
-    // coarse work units
+    // coarse work units (the buffers sized for the smallest unit the tuner tries)
     std::vector<int> cu_inst, cu_row0;
-    std::vector<int64_t> cu0(1, 0);
-    for (int b = 0; b < n_instances; ++b) {
-        for (int64_t r0 = 0; r0 < P.inst_ncn[b]; r0 += kCoarseRows) {
-            cu_inst.push_back(b);
-            cu_row0.push_back((int)r0);
-        }
-        cu0.push_back((int64_t)cu_inst.size());
-    }
+    std::vector<int64_t> cu0;
+    coarse_units(P, n_instances, opt.autotune ? 8 : kCoarseRows, cu_inst, cu_row0, cu0);
     h->inst_cfoff.assign(n_instances, 0);
     for (int b = 1; b < n_instances; ++b) h->inst_cfoff[b] = h->inst_cfoff[b - 1] + P.inst_ncf[b - 1];
     Params& p = h->prm;
@@ -2098,7 +2291,14 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     }
     p.n_inst = n_instances;
     p.n_sub = NS;
+    if (opt.autotune) coarse_units(P, n_instances, kCoarseRows, cu_inst, cu_row0, cu0);
+    if (!cu_inst.empty() && opt.autotune) {  // the default units into the larger buffers
+        cudaMemcpy(const_cast<int*>(p.cunit_inst), cu_inst.data(), cu_inst.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(const_cast<int*>(p.cunit_row0), cu_row0.data(), cu_row0.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(const_cast<int64_t*>(p.inst_cu0), cu0.data(), cu0.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    }
     p.n_cunits = (int64_t)cu_inst.size();
+    p.coarse_rows = kCoarseRows;
     p.maxit = opt.maxit;
     p.max_ng = std::max(P.max_ng, 1);
     p.max_in_post = std::max(P.max_in_post, 1);
@@ -2129,38 +2329,26 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     int nb = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, h->smem);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-    const int64_t want = std::max<int64_t>(NS, p.n_cunits);
-    h->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nb * nsm, want));
+    h->grid = solve_grid(nb, nsm, NS, p.n_cunits);
     if (nb <= 0) {
         bddc_destroy(h);
         return BDDC_E_CUDA;
     }
     {
-        // contiguous subdomain ranges per warp at equal fractions of the
-        // summed cost n_Gamma^2 + 4096: the operators S and F (n_Gamma^2)
-        // plus a fixed latency cost of a unit (gathers, reductions,
-        // arrivals) worth a 64-dof interface.  Measured on GB300: the
-        // irregular 3-8-cell boxes of the 60x220x85 grid 153 -> 109 ms per
-        // solve against equal subdomain counts; pure n_Gamma^2 made the
-        // regular partitions 3-13 % slower, this weight within 1 %.
-        const int64_t W = (int64_t)h->grid * kWarps;
-        std::vector<double> pre(NS + 1, 0.0);
-        for (int64_t s = 0; s < NS; ++s) pre[s + 1] = pre[s] + (double)P.sub_ng[s] * P.sub_ng[s] + 4096.0;
-        std::vector<int64_t> ws(W + 1);
-        int64_t s = 0;
-        for (int64_t w = 0; w < W; ++w) {
-            const double target = pre[NS] * (double)w / (double)W;
-            while (s < NS && pre[s] < target) ++s;
-            ws[w] = s;
-        }
-        ws[W] = NS;
+        // warp ranges at the heuristic weight C = 4096, a fixed cost worth a
+        // 64-dof interface.  Measured on GB300: the irregular 3-8-cell boxes
+        // of the 60x220x85 grid 153 -> 109 ms per solve against equal
+        // subdomain counts; pure n_Gamma^2 made the regular partitions
+        // 3-13 % slower, this weight within 1 %.
         const int64_t* d = nullptr;
-        if (upload(h, ws, &d) != BDDC_OK) {
+        if (upload(h, warp_ranges(P, NS, (int64_t)h->grid * kWarps, kBalanceWeight), &d) != BDDC_OK) {
             bddc_destroy(h);
             return BDDC_E_OOM;
         }
         p.warp_sub0 = d;
     }
+    h->tuning.balance_weight = kBalanceWeight;
+    h->tuning.coarse_rows = kCoarseRows;
     cudaEventCreate(&h->ev0);
     cudaEventCreate(&h->ev1);
     if (cudaMallocHost((void**)&h->pin_st, sizeof(InstState) * n_instances) != cudaSuccess ||
@@ -2216,6 +2404,20 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         bddc_destroy(h);
         return BDDC_E_CUDA;
     }
+    if (opt.autotune) {
+        // the probes' constant data live in the staging buffers of bddc_solve
+        if (dalloc(h, (size_t)h->total_cells, &h->d_f) || dalloc(h, (size_t)h->total_faces, &h->d_bc) ||
+            dalloc(h, (size_t)h->total_faces, &h->d_flux) || dalloc(h, (size_t)h->total_cells, &h->d_p)) {
+            bddc_destroy(h);
+            return BDDC_E_OOM;
+        }
+        if (autotune_layout(h, const_cast<int64_t*>(p.warp_sub0), const_cast<int*>(p.cunit_inst),
+                            const_cast<int*>(p.cunit_row0), const_cast<int64_t*>(p.inst_cu0), nb, nsm) != BDDC_OK ||
+            cudaGetLastError() != cudaSuccess) {
+            bddc_destroy(h);
+            return BDDC_E_CUDA;
+        }
+    }
     *out = h;
     return BDDC_OK;
 }
@@ -2229,6 +2431,12 @@ int bddc_sizes(const bddc_handle* h, int* n_instances, int64_t* n_interface, int
     if (n_instances) *n_instances = h->n_inst;
     if (n_interface) *n_interface = h->P.n_gamma;
     if (n_subdomains) *n_subdomains = h->P.n_sub;
+    return BDDC_OK;
+}
+
+int bddc_get_tuning(const bddc_handle* h, bddc_tuning* out) {
+    if (!h || !out) return BDDC_E_INVALID_ARG;
+    *out = h->tuning;
     return BDDC_OK;
 }
 

@@ -29,7 +29,7 @@ namespace bddc {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kCoarseRows = 16;             // coarse rows per work unit
+constexpr int kCoarseRows = 16;             // coarse rows per work unit (default; Params::coarse_rows)
 constexpr long long kBarrierWaitNs = 10000000000LL;  // a grid-barrier wait past 10 s is an error
 constexpr int kActMaxInst = 4096;           // largest batch whose CG phases are rebalanced over active instances
 
@@ -109,7 +109,9 @@ struct Params {
     const double* slot_fk;
     const int *slot_fopp, *slot_fcell;
     // coarse units (inst_cu0: first unit of each instance, n_inst + 1 entries)
+    // of coarse_rows rows each
     int64_t n_cunits;
+    int coarse_rows;
     const int *cunit_inst, *cunit_row0;
     const int64_t* inst_cu0;
     // active-instance snapshots (per CTA, in shared memory): 0 = off (one

@@ -189,7 +189,7 @@ __device__ void mx_coarse(const Params& p, int64_t u, bool step1, double* rhs_ar
     const uint64_t pol = l2_stream_policy();
     const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t r0 = p.cunit_row0[u];
-    const int64_t r1 = (r0 + kCoarseRows < ncn) ? r0 + kCoarseRows : ncn;
+    const int64_t r1 = (r0 + p.coarse_rows < ncn) ? r0 + p.coarse_rows : ncn;
     float2* wc = V2(p.wc);
     for (int64_t row = r0 + wi; row < r1; row += kWarps) {
         const float2* kr = K + row * ncn;

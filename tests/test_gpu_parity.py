@@ -423,3 +423,48 @@ def test_msmfem_and_explicit_constraints_match_oracle(bddc, case):
     srv.close()
     assert rc == bddc.BDDC_OK and its_s == itx
     assert np.array_equal(fs, fx) and np.array_equal(ps, px)
+
+
+@pytest.mark.parametrize("kind,precision", [("batch_dense", 0), ("batch_dense", 1), ("single_sparse", 0)])
+def test_autotuned_layout_is_bitwise_equal_and_cached(bddc, kind, precision):
+    """bddc_options.autotune: the probe-chosen work layout (the warp ranges'
+    weight, the dense coarse unit size) decides which warp or CTA does a
+    subdomain's or a coarse row's work, not the order of any sum, so the
+    solve is bitwise equal to the heuristic layout's.  The report names one
+    of the candidates with its probe times; a second setup with the same
+    signature takes the choice from the process cache."""
+    if kind == "batch_dense":
+        pbs = [make_config("c2", seed=2190 + i) for i in range(6)]
+        extra = dict(coarse_solver=bddc.BDDC_COARSE_DENSE)
+    else:
+        pbs = [_irregular3d()]
+        extra = dict(coarse_solver=bddc.BDDC_COARSE_SPARSE)
+    stream = torch.cuda.current_stream().cuda_stream
+    f = np.concatenate([pb.f for pb in pbs])
+    bc = np.concatenate([pb.bc_value for pb in pbs])
+
+    def run(autotune):
+        opt = bddc.default_options(tau=4.0, precision=precision, autotune=autotune, **extra)
+        h = bddc.setup(pbs, opt, stream=stream)
+        flux = torch.empty(len(bc), dtype=torch.float64, device="cuda")
+        pres = torch.empty(len(f), dtype=torch.float64, device="cuda")
+        its = torch.empty(len(pbs), dtype=torch.int32, device="cuda")
+        h.solve(_dev(f), _dev(bc), 1e-10, flux, pres, its)
+        torch.cuda.synchronize()
+        t = h.tuning()
+        rep = (t.tuned, t.from_cache, t.balance_weight, t.coarse_rows, t.probe_ms, t.probe_ms_default)
+        out = flux.cpu().numpy(), pres.cpu().numpy(), its.cpu().numpy(), rep
+        h.close()
+        return out
+
+    heur, tuned, again = run(0), run(1), run(1)
+    assert heur[3][:4] == (0, 0, 4096.0, 16)
+    assert tuned[3][0] == 1 and tuned[3][1] == 0
+    assert tuned[3][2] in (0.0, 1024.0, 4096.0, 16384.0, 65536.0)
+    assert tuned[3][3] in ((8, 16, 32) if kind == "batch_dense" else (16,))
+    assert 0.0 < tuned[3][4] <= tuned[3][5]
+    assert again[3][:2] == (1, 1) and again[3][2:] == tuned[3][2:]
+    for out in (tuned, again):
+        assert np.array_equal(out[2], heur[2])
+        assert np.array_equal(out[0], heur[0])
+        assert np.array_equal(out[1], heur[1])

@@ -6,6 +6,7 @@ The host setup is read back through bddc_host_setup_* and replayed in NumPy
 result must match the oracle.
 """
 
+import ctypes as C
 import os
 import re
 
@@ -150,6 +151,18 @@ def test_setup_rejects_invalid_inputs():
         bddc.HostSetup([bad])
     assert e.value.code == bddc.BDDC_E_INVALID_ARG
     assert bddc.HostSetup([pb]) is not None
+
+
+def test_setup_rejects_invalid_autotune_option_and_get_tuning_null():
+    """bddc_options.autotune takes 0 or 1 (checked before any device work);
+    bddc_get_tuning rejects a null handle."""
+    o = bddc.default_options(autotune=2)
+    with pytest.raises(bddc.BDDCError) as e:
+        bddc.setup([make_config("c1")], o)
+    assert e.value.code == bddc.BDDC_E_INVALID_ARG
+    assert bddc.default_options().autotune == 0
+    t = bddc.bddc_tuning()
+    assert bddc.lib.bddc_get_tuning(None, C.byref(t)) == bddc.BDDC_E_INVALID_ARG
 
 
 def test_setup_without_gpu_reports_cuda_error_not_crash():
