@@ -153,10 +153,11 @@ struct LocalMapsBatch {
     std::vector<double> cs;
     // per interface dof: its cell, axis and side (0 lower, 1 upper)
     std::vector<int> gcell, gaxis, gside;
-    // per interior dof, in chain order: interior index and Thomas factors;
-    // per chain (o_ch, n_chains + 1 entries per subdomain): start position
+    // per interior dof, in chain order: interior index and Thomas factors
+    // (rdfac: reciprocals of the pivots); per chain (o_ch, n_chains + 1
+    // entries per subdomain): start position
     std::vector<int> order, cstart;
-    std::vector<double> dfac, lfac, off;
+    std::vector<double> rdfac, lfac, off;
     // outputs, in the layouts of the host setup
     std::vector<int64_t> o_S, o_Gpre, o_Gpost;
     std::vector<double> S, GpreT;

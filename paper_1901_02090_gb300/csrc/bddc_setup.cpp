@@ -531,14 +531,22 @@ SetupResult local_maps(const Inst& I, Sub& S, bool pressure_scaling) {
             for (int r = 0; r < nc; ++r) ypm[(size_t)r * ncol + j] -= col[r];
         }
         lu_solve(nq, Qm.data(), piv, ypm.data(), ncol);
+        // y_u = A_II^{-1} (x_u - dB_I^T y_p): the sparse transpose and a
+        // second chain solve (n_i work) in place of the dense product with
+        // Y (n_i n_c work)
         for (int j = 0; j < ncol; ++j) {
             double* t = &yu[(size_t)j * ni];
+            for (int e = 0; e < ni; ++e) t[e] = xu[(size_t)j * ni + e];
             for (int r = 0; r < nc; ++r) {
                 const double yp = ypm[(size_t)r * ncol + j];
                 if (yp == 0.0) continue;
-                const double* y = &Y[(size_t)r * ni];
-                for (int e = 0; e < ni; ++e) t[e] -= y[e] * yp;
+                for (int a = 0; a < dim; ++a) {
+                    const int l = S.clo[(size_t)r * dim + a], h = S.chi[(size_t)r * dim + a];
+                    if (l >= ng) t[l - ng] -= d * yp;   // B[c, lower] = +1
+                    if (h >= ng) t[h - ng] += d * yp;   // B[c, upper] = -1
+                }
             }
+            chain_solve(ch, t);
         }
     };
     std::vector<double> YU, YPM;
@@ -1082,7 +1090,7 @@ SetupResult device_local_maps(std::vector<Inst>& I, const std::vector<std::pair<
         B.gside.insert(B.gside.end(), pre[t].gside.begin(), pre[t].gside.end());
         const Chains& ch = pre[t].ch;
         B.order.insert(B.order.end(), ch.order.begin(), ch.order.end());
-        B.dfac.insert(B.dfac.end(), ch.dfac.begin(), ch.dfac.end());
+        for (double dv : ch.dfac) B.rdfac.push_back(1.0 / dv);  // the device multiplies
         B.lfac.insert(B.lfac.end(), ch.lfac.begin(), ch.lfac.end());
         B.off.insert(B.off.end(), ch.off.begin(), ch.off.end());
         B.cstart.insert(B.cstart.end(), ch.start.begin(), ch.start.end());

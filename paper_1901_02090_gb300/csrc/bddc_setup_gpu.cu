@@ -9,7 +9,8 @@
 // host); eliminating it leaves the dense pressure Schur complement
 //     Q = [[-dB_I A_II^{-1} dB_I^T, v], [v^T, 0]]      (n_c + 1 square)
 // which is LU-factored with partial pivoting.  All right-hand sides are
-// solved together and refined against the exact sparse local
+// solved together (the interior fluxes last, u = A_II^{-1}(x_u - dB_I^T p),
+// two chain solves per column) and refined against the exact sparse local
 // operator (the elimination loses accuracy in proportion to the
 // permeability contrast).  This is the algorithm of local_maps in
 // bddc_setup.cpp step by step (kLocalRefinements steps of refinement);
@@ -43,7 +44,7 @@ struct LmView {
     const double* cs;
     const int *gcell, *gaxis, *gside;
     const int *order, *cstart;
-    const double *dfac, *lfac, *off;
+    const double *rdfac, *lfac, *off;  // Thomas factors (rdfac: pivot reciprocals)
     double *S, *GpreT, *GpostT;
     int* status;
     // scratch, per launch-local subdomain t: offsets o_*[t]
@@ -75,13 +76,13 @@ __device__ __forceinline__ Dims dims(const LmView& v) {
 __device__ void chain_solve(const LmView& v, const Dims& q, double* x, int stride) {
     const int64_t ob = v.o_ni[q.s];
     const int* ord = v.order + ob;
-    const double *lf = v.lfac + ob, *df = v.dfac + ob, *of = v.off + ob;
+    const double *lf = v.lfac + ob, *rd = v.rdfac + ob, *of = v.off + ob;
     for (int64_t c = v.o_ch[q.s]; c + 1 < v.o_ch[q.s + 1]; ++c) {
         const int b = v.cstart[c], e = v.cstart[c + 1];
         for (int p = b + 1; p < e; ++p) x[(int64_t)ord[p] * stride] -= lf[p] * x[(int64_t)ord[p - 1] * stride];
-        x[(int64_t)ord[e - 1] * stride] /= df[e - 1];
+        x[(int64_t)ord[e - 1] * stride] *= rd[e - 1];
         for (int p = e - 2; p >= b; --p)
-            x[(int64_t)ord[p] * stride] = (x[(int64_t)ord[p] * stride] - of[p] * x[(int64_t)ord[p + 1] * stride]) / df[p];
+            x[(int64_t)ord[p] * stride] = (x[(int64_t)ord[p] * stride] - of[p] * x[(int64_t)ord[p + 1] * stride]) * rd[p];
     }
 }
 
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_Q(LmView v) {
 
 // in-place LU of Q with partial pivoting (the pivot is the first row of
 // largest magnitude in the column, as on the host); multipliers in the
-// strict lower triangle, piv[k] the row swapped with k
+// strict lower triangle, U above it with the reciprocals of its pivots on
+// the diagonal, piv[k] the row swapped with k
 __global__ void __launch_bounds__(kLmThreads) k_lm_lu(LmView v) {
     extern __shared__ double lcol[];  // multipliers of the current step
     __shared__ int piv_sh, bad_sh;
@@ -195,6 +197,8 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_lu(LmView v) {
         }
         __syncthreads();
     }
+    // the diagonal of U is kept as its reciprocals (the solves multiply)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * n + i] = 1.0 / A[(int64_t)i * n + i];
 }
 
 // right-hand sides: interface column j < ng is -K_I,G e_j (the other flux
@@ -223,8 +227,8 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_rhs(LmView v) {
 }
 
 // solve K_I [yu; yp] = [xu; xp] for every column (one column per thread):
-// interior elimination, LU solve of the pressure Schur complement, back
-// substitution of the interior fluxes
+// interior elimination, LU solve of the pressure Schur complement, the
+// interior fluxes from a second chain solve
 __global__ void __launch_bounds__(kLmThreads) k_lm_solve(LmView v, const double* xu_all, const double* xp_all,
                                                           double* yu_all, double* yp_all) {
     const Dims q = dims(v);
@@ -233,7 +237,6 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_solve(LmView v, const double*
     const double* xp = xp_all + v.o_P[q.t];
     double* yu = yu_all + v.o_U[q.t];
     double* yp = yp_all + v.o_P[q.t];
-    const double* Y = v.Y + v.o_Y[q.t];
     const double* LU = v.Q + v.o_Q[q.t];
     const int* piv = v.piv + v.o_piv[q.t];
     const int n = q.nq, nc = q.ncol;
@@ -264,16 +267,23 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_solve(LmView v, const double*
                 const double uu = LU[(int64_t)i * n + k];
                 if (uu != 0.0) acc -= uu * pp[(int64_t)k * nc];
             }
-            pp[(int64_t)i * nc] = acc * (1.0 / LU[(int64_t)i * n + i]);
+            pp[(int64_t)i * nc] = acc * LU[(int64_t)i * n + i];  // the stored reciprocal
         }
-        // u_e -= sum_r Y(e, r) y_r, accumulated in a register per entry (the
-        // same order over r for every entry; one store per entry)
-        for (int e = 0; e < q.ni; ++e) {
-            const double* Ye = Y + (int64_t)e * q.nc;
-            double acc = u[(int64_t)e * nc];
-            for (int r = 0; r < q.nc; ++r) acc -= Ye[r] * pp[(int64_t)r * nc];
-            u[(int64_t)e * nc] = acc;
+        // u = A_II^{-1} (x_u - dB_I^T y_p): the sparse transpose and a second
+        // chain solve (n_i work per column) in place of the dense product
+        // with Y (n_i n_c work per column)
+        for (int e = 0; e < q.ni; ++e) u[(int64_t)e * nc] = xu[(int64_t)e * nc + j];
+        const int64_t cb0 = v.o_cell[q.s] * 3;
+        for (int r = 0; r < q.nc; ++r) {
+            const double yr = pp[(int64_t)r * nc];
+            if (yr == 0.0) continue;
+            for (int a = 0; a < q.dim; ++a) {
+                const int l = v.clo[cb0 + 3 * r + a], h = v.chi[cb0 + 3 * r + a];
+                if (l >= q.ng) u[(int64_t)(l - q.ng) * nc] -= q.d * yr;  // B[c, lower] = +1
+                if (h >= q.ng) u[(int64_t)(h - q.ng) * nc] += q.d * yr;  // B[c, upper] = -1
+            }
         }
+        chain_solve(v, q, u, nc);
     }
 }
 
@@ -424,7 +434,7 @@ int local_maps_device(LocalMapsBatch& B, std::string& err) {
         v.gside = m.upload(B.gside, st);
         v.order = m.upload(B.order, st);
         v.cstart = m.upload(B.cstart, st);
-        v.dfac = m.upload(B.dfac, st);
+        v.rdfac = m.upload(B.rdfac, st);
         v.lfac = m.upload(B.lfac, st);
         v.off = m.upload(B.off, st);
         v.S = m.alloc<double>(B.S.size());
