@@ -323,7 +323,7 @@ def serving_run(args, rank, rate):
     gaps = np.random.default_rng(7 + rank + int(rate)).exponential(1.0 / rate, size=n)
     srv = bddc.Server(bddc.default_options(tau=args.tau, precision=bddc.BDDC_PREC_FP32),
                       hbm_budget_bytes=16 << 30, max_batch=64)
-    pending, lat, its, batches, setup_ms, queue_ms = [], [], [], set(), [], []
+    pending, lat, its, batches, setup_ms, queue_ms, solve_ms = [], [], [], set(), [], [], []
     t0 = time.perf_counter()
     t_next = t0
     for i, pb in enumerate(pbs):
@@ -339,16 +339,27 @@ def serving_run(args, rank, rate):
         lat.append(info.latency_ms)
         setup_ms.append(info.setup_ms)
         queue_ms.append(info.queue_ms)
+        solve_ms.append(info.solve_ms)
         its.append(it)
         batches.add(info.batch_id)
     wall = time.perf_counter() - t0
     peak = srv.info().device_bytes_peak
     srv.close()
     lat = np.array(lat)
+    q = max(1, n // 4)
+    span = float(np.sum(gaps))
     return {"value": n / wall, "unit": "solves/s", "requests": n, "arrival_rate_per_s": rate,
-            "offered_span_s": float(np.sum(gaps)), "wall_s": wall,
+            # the seeded sample's own rate (n over its arrival span); wall_s adds
+            # the last requests' latency (the drain), so value < offered_rate
+            # even for a loop that keeps up
+            "offered_rate_per_s": n / span, "offered_span_s": span, "wall_s": wall,
+            # keeping up: the queue does not grow over the stream
+            "p50_latency_first_quarter_ms": float(np.percentile(lat[:q], 50)),
+            "p50_latency_last_quarter_ms": float(np.percentile(lat[-q:], 50)),
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
             "mean_setup_ms": float(np.mean(setup_ms)), "mean_queue_ms": float(np.mean(queue_ms)),
+            # the launch a request rode in (the unit that launch-boundary admission waits for)
+            "mean_solve_ms": float(np.mean(solve_ms)),
             "failed": int(failed), "batches": len(batches), "mean_batch": n / max(1, len(batches)),
             "iterations_mean": float(np.mean(its)), "device_bytes_peak": int(peak)}
 

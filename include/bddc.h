@@ -297,24 +297,28 @@ int bddc_subassembled_apply_noalloc(int n_sub, const int* ng, const int64_t* slo
  * n_Gamma^2 + balance_weight (the operator blocks plus a fixed latency per
  * subdomain); each CTA takes units of coarse_rows rows of the dense coarse
  * inverse.  With bddc_options.autotune the setup times the persistent kernel
- * itself on the handle's operators (six CG iterations on a constant
- * right-hand side, the minimum of two launches) for the weights 0, 1024,
- * 4096, 16384 and 65536 and then, for the dense coarse solver, the unit
- * sizes 8, 16 and 32 rows (those that leave the launch grid unchanged), and
- * keeps the fastest, the heuristic winning ties within 1 %.  The choice is
- * cached per signature (launch grid, batch size, interface and constraint
- * sizes of every subdomain, coarse sizes, precision, form) for later setups
- * of the process.  A probe that fails to launch or times out leaves the
- * heuristic in place.  Without autotune: 4096 and 16.  Tuning allocates the
- * host-array staging buffers of bddc_solve at setup.  Returns BDDC_OK, or
- * BDDC_E_INVALID_ARG for a null argument. */
+ * itself on the handle's operators for every candidate: the weights 4096
+ * (the heuristic), 0, 1024, 16384 and 65536, crossed, for the dense coarse
+ * solver, with the unit sizes 16, 8 and 32 rows (those that leave the launch
+ * grid unchanged).  A candidate is timed by probe launches of 2 and 8 CG
+ * iterations on a constant right-hand side, in two round-robin rounds after
+ * three warm-up launches, the minimum per candidate and length; the
+ * candidates are compared by the predicted time of a 30-iteration solve
+ * (the 2-iteration time plus 28 times the cost per iteration), and the
+ * heuristic wins ties within 2 %.  The choice is cached per signature
+ * (launch grid, batch size, interface and constraint sizes of every
+ * subdomain, coarse sizes, precision, form) for later setups of the process.
+ * A probe that fails to launch or times out leaves the heuristic in place.
+ * Without autotune: 4096 and 16.  Tuning allocates the host-array staging
+ * buffers of bddc_solve at setup.  Returns BDDC_OK, or BDDC_E_INVALID_ARG
+ * for a null argument. */
 typedef struct {
     int tuned;                /* 1: chosen by probe solves (or taken from the cache), 0: heuristic */
     int from_cache;           /* 1: the choice of an earlier setup with the same signature */
     double balance_weight;    /* C of the warp ranges */
     int coarse_rows;          /* rows of a dense-coarse work unit */
-    double probe_ms;          /* the chosen layout's probe time (0 if not tuned) */
-    double probe_ms_default;  /* the heuristic layout's probe time (0 if not tuned) */
+    double probe_ms;          /* the chosen layout's predicted 30-iteration solve time (0 if not tuned) */
+    double probe_ms_default;  /* the heuristic layout's predicted time (0 if not tuned) */
 } bddc_tuning;
 int bddc_get_tuning(const bddc_handle* h, bddc_tuning* out);
 

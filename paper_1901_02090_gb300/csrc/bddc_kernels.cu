@@ -1900,7 +1900,11 @@ int solve_grid(int nb, int nsm, int64_t n_sub, int64_t n_cunits) {
 }
 
 constexpr double kBalanceWeight = 4096.0;  // C of the heuristic warp ranges
-constexpr int kProbeIters = 6;             // CG iterations of a tuning probe
+// tuning probes: launches of kProbeShort and kProbeLong CG iterations give
+// the once-per-solve part and the cost per iteration; layouts are compared
+// by the predicted time of a kProbeNominal-iteration solve
+constexpr int kProbeShort = 2, kProbeLong = 8, kProbeNominal = 30;
+constexpr int kProbeRounds = 2;  // rounds over all candidates (minimum per candidate)
 
 // the layouts chosen by earlier tuned setups of this process, by signature
 std::mutex g_tune_mu;
@@ -1933,11 +1937,11 @@ uint64_t tune_signature(const bddc_handle* h, int grid) {
 }
 
 // device time (ms) of one probe launch of the persistent kernel with the
-// layout in p: kProbeIters CG iterations (tolerance 0) on the handle's
-// constant probe data; -1 on a launch error or a barrier timeout
-float probe_launch(bddc_handle* h, Params p) {
+// layout in p: `iters` CG iterations (tolerance 0) on the handle's constant
+// probe data; -1 on a launch error or a barrier timeout
+float probe_launch(bddc_handle* h, Params p, int iters) {
     cudaStream_t st = h->stream;
-    p.maxit = std::min(kProbeIters, p.maxit);  // the CG history's pitch stays within the handle's
+    p.maxit = std::min(iters, p.maxit);  // the CG history's pitch stays within the handle's
     p.tol = 0.0;
     p.f_in = h->d_f;
     p.bc_in = h->d_bc;
@@ -1962,12 +1966,17 @@ float probe_launch(bddc_handle* h, Params p) {
     return ms;
 }
 
-// Autotuning of the work layout (bddc_options.autotune): time probe launches
-// of the persistent kernel for the warp-range weights C and, with the dense
-// coarse solver, the unit sizes; keep the fastest (the heuristic wins ties
-// within 1 %).  ws_dev is the warp-range buffer (grid * kWarps + 1 entries),
-// cu_* the unit buffers, sized for the smallest unit.  Returns BDDC_OK or a
-// CUDA error; the handle keeps the heuristic layout when a probe fails.
+// Autotuning of the work layout (bddc_options.autotune).  Candidates: the
+// warp-range weights C and, with the dense coarse solver, the coarse unit
+// sizes that leave the launch grid unchanged.  Each candidate is timed by
+// probe launches of kProbeShort and kProbeLong iterations, in kProbeRounds
+// round-robin rounds after a warm-up (so that a drift of the clocks during
+// the tuning favours no candidate), the minimum per candidate and length.
+// The predicted time of a kProbeNominal-iteration solve decides; the
+// heuristic wins ties within 2 %.  ws_dev is the warp-range buffer
+// (grid * kWarps + 1 entries), cu_* the unit buffers, sized for the smallest
+// unit.  Returns BDDC_OK or a CUDA error; the handle keeps the heuristic
+// layout when a probe fails.
 int autotune_layout(bddc_handle* h, int64_t* ws_dev, int* cu_inst_dev, int* cu_row0_dev, int64_t* cu0_dev, int nb,
                     int nsm) {
     const Packed& P = h->P;
@@ -2004,53 +2013,56 @@ int autotune_layout(bddc_handle* h, int64_t* ws_dev, int* cu_inst_dev, int* cu_r
         if (!set_weight(T.balance_weight) || !set_rows(T.coarse_rows)) return BDDC_E_CUDA;
         return BDDC_OK;
     }
-    cudaMemset(h->d_f, 0x3f, (size_t)h->total_cells * sizeof(double));  // a constant 4.8e-4 in every cell
-    cudaMemset(h->d_bc, 0, (size_t)h->total_faces * sizeof(double));
-    if (cudaDeviceSynchronize() != cudaSuccess) return BDDC_E_CUDA;
-    auto time_layout = [&]() -> float {
-        float best = -1.0f;
-        for (int r = 0; r < 2; ++r) {
-            const float ms = probe_launch(h, p);
-            if (ms < 0.0f) return -1.0f;
-            best = best < 0.0f ? ms : std::min(best, ms);
-        }
-        return best;
-    };
-    if (probe_launch(h, p) < 0.0f) return BDDC_OK;  // warm-up; on failure keep the heuristic
-    const float t_def = time_layout();
-    if (t_def < 0.0f) return BDDC_OK;
-    double bestC = kBalanceWeight;
-    int best_rows = p.coarse_rows;
-    float best_t = t_def;
-    for (double C : {0.0, 1024.0, 16384.0, 65536.0}) {
-        if (!set_weight(C)) return BDDC_E_CUDA;
-        const float t = time_layout();
-        if (t >= 0.0f && t < 0.99f * best_t) {
-            best_t = t;
-            bestC = C;
-        }
-    }
-    if (!set_weight(bestC)) return BDDC_E_CUDA;
-    if (!P.coarse_sparse) {
+    // candidates, the heuristic first
+    std::vector<std::pair<double, int>> cand;
+    const double weights[] = {kBalanceWeight, 0.0, 1024.0, 16384.0, 65536.0};
+    std::vector<int> rows_list{kCoarseRows};
+    if (!P.coarse_sparse)
         for (int rows : {8, 32}) {
             std::vector<int> a, b;
             std::vector<int64_t> c;
             coarse_units(P, h->n_inst, rows, a, b, c);
-            if (solve_grid(nb, nsm, NS, (int64_t)a.size()) != h->grid) continue;  // the warp ranges would change
-            if (!set_rows(rows)) return BDDC_E_CUDA;
-            const float t = time_layout();
-            if (t >= 0.0f && t < 0.99f * best_t) {
-                best_t = t;
-                best_rows = rows;
-            }
+            if (solve_grid(nb, nsm, NS, (int64_t)a.size()) == h->grid) rows_list.push_back(rows);
         }
-        if (!set_rows(best_rows)) return BDDC_E_CUDA;
-    }
+    for (int rows : rows_list)
+        for (double C : weights) cand.emplace_back(C, rows);
+    cudaMemset(h->d_f, 0x3f, (size_t)h->total_cells * sizeof(double));  // a constant 4.8e-4 in every cell
+    cudaMemset(h->d_bc, 0, (size_t)h->total_faces * sizeof(double));
+    if (cudaDeviceSynchronize() != cudaSuccess) return BDDC_E_CUDA;
+    auto restore = [&]() -> int {
+        return set_weight(kBalanceWeight) && set_rows(kCoarseRows) ? BDDC_OK : BDDC_E_CUDA;
+    };
+    for (int r = 0; r < 3; ++r)  // warm-up
+        if (probe_launch(h, p, kProbeLong) < 0.0f) return restore();
+    const size_t n = cand.size();
+    std::vector<float> t_short(n, 1e30f), t_long(n, 1e30f);
+    int cur_rows = kCoarseRows;
+    for (int round = 0; round < kProbeRounds; ++round)
+        for (size_t k = 0; k < n; ++k) {
+            const size_t c = (k + round * (n / 2 + 1)) % n;  // another order each round
+            if (!set_weight(cand[c].first)) return BDDC_E_CUDA;
+            if (cand[c].second != cur_rows) {
+                if (!set_rows(cand[c].second)) return BDDC_E_CUDA;
+                cur_rows = cand[c].second;
+            }
+            const float a = probe_launch(h, p, kProbeShort), b = probe_launch(h, p, kProbeLong);
+            if (a < 0.0f || b < 0.0f) return restore();
+            t_short[c] = std::min(t_short[c], a);
+            t_long[c] = std::min(t_long[c], b);
+        }
+    auto predict = [&](size_t c) {
+        const float per_it = std::max(0.0f, (t_long[c] - t_short[c]) / (float)(kProbeLong - kProbeShort));
+        return t_short[c] + (float)(kProbeNominal - kProbeShort) * per_it;
+    };
+    size_t best = 0;  // the heuristic
+    for (size_t c = 1; c < n; ++c)
+        if (predict(c) < 0.98f * predict(0) && predict(c) < predict(best)) best = c;
+    if (!set_weight(cand[best].first) || !set_rows(cand[best].second)) return BDDC_E_CUDA;
     T.tuned = 1;
-    T.balance_weight = bestC;
-    T.coarse_rows = best_rows;
-    T.probe_ms = best_t;
-    T.probe_ms_default = t_def;
+    T.balance_weight = cand[best].first;
+    T.coarse_rows = cand[best].second;
+    T.probe_ms = predict(best);
+    T.probe_ms_default = predict(0);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache.emplace_back(sig, T);
     return BDDC_OK;
