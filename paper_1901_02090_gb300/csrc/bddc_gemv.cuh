@@ -63,17 +63,19 @@ __device__ __forceinline__ void gemv_column(const T* __restrict__ M, int n, cons
     for (; j < j1; ++j) a.add(__ldg(M + (int64_t)j * n + o), w, j);
 }
 
-// out(o, y_o) for o = 0..n-1, each o on one lane; called by the whole warp
+// out(o, y_o) for the outputs o = ob..oe-1 of the n x n operator, each o on
+// one lane; called by the whole warp
 template <class T, class Out>
-__device__ __forceinline__ void gemv_warp(const T* __restrict__ M, int n, const WarpSm& w, Out&& out) {
+__device__ __forceinline__ void gemv_warp_range(const T* __restrict__ M, int n, int ob, int oe, const WarpSm& w,
+                                                Out&& out) {
     const int l = threadIdx.x & 31;
-    const int full = n & ~31;
-    for (int o0 = 0; o0 < full; o0 += 32) {
+    const int full = ob + ((oe - ob) & ~31);
+    for (int o0 = ob; o0 < full; o0 += 32) {
         GAcc<T> a;
         gemv_column(M, n, w, o0 + l, 0, n, a);
         out(o0 + l, a.value());
     }
-    const int r = n - full;
+    const int r = oe - full;
     if (r == 0) return;
     int R = 1;
     while (R < r) R <<= 1;
@@ -84,4 +86,10 @@ __device__ __forceinline__ void gemv_warp(const T* __restrict__ M, int n, const 
     gemv_column(M, n, w, o, (n * g) / G, (n * (g + 1)) / G, a);
     for (int off = R; off < 32; off <<= 1) a.shfl_add(off);
     if (g == 0 && e < r) out(o, a.value());
+}
+
+// out(o, y_o) for o = 0..n-1
+template <class T, class Out>
+__device__ __forceinline__ void gemv_warp(const T* __restrict__ M, int n, const WarpSm& w, Out&& out) {
+    gemv_warp_range(M, n, 0, n, w, static_cast<Out&&>(out));
 }

@@ -174,13 +174,15 @@ __device__ void cg_alpha(const Params& p, int b, int k, double dq) {
     }
 }
 
-// count the arrival of n subdomains of instance b whose partials of kind
-// ctr this warp has stored; the completing warp publishes the total and
-// takes the scalar step.  A warp counts all its consecutive subdomains of
-// an instance with one atomic (it usually holds several per phase).
+// count the arrival of n units of instance b whose partials of kind ctr
+// this warp has stored (subdomains; operator-apply units for kCtrDQ); the
+// completing warp publishes the total (the partials summed in unit order)
+// and takes the scalar step.  A warp counts all its consecutive units of an
+// instance with one atomic (it usually holds several per phase).
 __device__ void publish_total(const Params& p, int b, int n, int ctr, int k = 0, bool with_a = false,
                               bool fp64_correction = false) {
-    const int64_t s0 = p.inst_s0[b], s1 = p.inst_s1[b];
+    const bool du = ctr == kCtrDQ;
+    const int64_t s0 = du ? p.inst_du0[b] : p.inst_s0[b], s1 = du ? p.inst_du0[b + 1] : p.inst_s1[b];
     int* cnt = p.inst_cnt + (int64_t)b * kCounters + ctr;
     int last = 0;
     __syncwarp();
@@ -797,9 +799,11 @@ __device__ bool ph_prolong(const Params& p, int64_t s, WarpSm w) {
     return true;
 }
 
-// direction update d = z + beta d and operator apply q = S d + B_0^T d_p
+// direction update d = z + beta d and operator apply q = S d + B_0^T d_p,
+// for the outputs [ob, oe) of operator-apply unit u of subdomain s (the unit
+// with ob = 0 also stores the subdomain's new direction)
 template <class PR>
-__device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm w) {
+__device__ bool ph_dirop(const Params& p, int64_t u, int64_t s, int ob, int oe, int k, WarpSm w) {
     using S_t = typename PR::S_t;
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
@@ -816,22 +820,22 @@ __device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm w) {
         const int gi = p.slot_g[so + kk];
         const double z = __ldcg(p.zl + so + kk) + (pt >= 0 ? __ldcg(p.zl + pt) : 0.0);
         const double dn = (k == 0) ? z : z + beta * __ldcg(dold + gi);
-        if (slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
+        if (ob == 0 && slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
         w.x[kk] = dn;
     }
     const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
-    if (l == 0) dpnew[s] = dpn;
+    if (l == 0 && ob == 0) dpnew[s] = dpn;
     __syncwarp();
     if constexpr (PR::kMixed) split_pairs(w, ng);
     const S_t* S = reinterpret_cast<const S_t*>(p.S) + p.off_S[s];
     double dq = 0.0;
-    gemv_warp(S, ng, w, [&](int kk, typename GAcc<S_t>::value_type y) {
+    gemv_warp_range(S, ng, ob, oe, w, [&](int kk, typename GAcc<S_t>::value_type y) {
         const double q = to_double(y) + p.slot_dsig[so + kk] * dpn;
         p.ql[so + kk] = q;
         dq += w.x[kk] * q;
     });
     dq = warp_sum(dq);
-    if (l == 0) p.part_dq[s] = dq;
+    if (l == 0) p.part_dq[u] = dq;
     __syncwarp();
     return true;
 }
@@ -847,7 +851,7 @@ __device__ bool ph_dirop(const Params& p, int64_t s, int k, WarpSm w) {
 // +p_K if the face is K's lower face, -p_K if its upper face.  Equal to
 // S^i d + d_s sigma p_0 up to rounding (the condensed form).
 template <class PR>
-__device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm w) {
+__device__ bool ph_dirop_full(const Params& p, int64_t u, int64_t s, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -899,7 +903,7 @@ __device__ bool ph_dirop_full(const Params& p, int64_t s, int k, WarpSm w) {
         dq += ue * q;
     }
     dq = warp_sum(dq);
-    if (l == 0) p.part_dq[s] = dq;
+    if (l == 0) p.part_dq[u] = dq;  // one unit per subdomain in the full form
     __syncwarp();
     return true;
 }
@@ -1348,11 +1352,45 @@ __global__ void __launch_bounds__(kThreads, 4) bddc_solve_kernel(Params p) {
         } else if (__ldcg(p.n_active) <= 0) {
             break;
         }
-        cg_phase(kCtrDQ, k, [&](int64_t s) -> bool {
-            if constexpr (MX) return mx_dirop(p, s, k, wsm());
-            else if constexpr (PR::kFull) return ph_dirop_full<PR>(p, s, k, wsm());
-            else return ph_dirop<PR>(p, s, k, wsm());
-        });
+        // DIROP over the operator-apply units: the warp's work-balanced unit
+        // range, or with g_partial_sh the units of its even share of the
+        // active instances' subdomains
+        {
+            int cur = -1, n = 0;
+            auto dirop_unit = [&](int64_t u) {
+                const int2 du = __ldg(p.dunit + u);
+                const int b = p.sub_inst[du.x];
+                if (b != cur) {
+                    if (n > 0) publish_total(p, cur, n, kCtrDQ, k, false, !MX);
+                    cur = b;
+                    n = 0;
+                }
+                bool ok;
+                if constexpr (MX) ok = mx_dirop(p, u, du.x, du.y >> 16, du.y & 0xffff, k, wsm());
+                else if constexpr (PR::kFull) ok = ph_dirop_full<PR>(p, u, du.x, k, wsm());
+                else ok = ph_dirop<PR>(p, u, du.x, du.y >> 16, du.y & 0xffff, k, wsm());
+                if (ok) ++n;
+            };
+            if (kBal && g_partial_sh) {
+                const int64_t A = act_area<PR::kFull>(p, smem_base)[p.act_n];
+                const int64_t W = (int64_t)gridDim.x * kWarps;
+                const int64_t wg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+                a = (A * wg) / W;
+                e = (A * (wg + 1)) / W;
+                for (int64_t x = a; x < e; ++x) {
+                    const int* act_sub = act_area<PR::kFull>(p, smem_base);
+                    const int b = act_find(act_sub, p.act_n, x);
+                    const int64_t sx = p.inst_s0[b] + (x - act_sub[b]);
+                    for (int64_t u = p.sub_du0[sx]; u < p.sub_du0[sx + 1]; ++u) dirop_unit(u);
+                }
+            } else {
+                const int64_t wg = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+                a = p.warp_du0[wg];
+                e = p.warp_du0[wg + 1];
+                for (int64_t u = a; u < e; ++u) dirop_unit(u);
+            }
+            if (n > 0) publish_total(p, cur, n, kCtrDQ, k, false, !MX);
+        }
         if (!phase_end(p, 8, nts)) return;
         cg_phase(kCtrRR, k, [&](int64_t s) -> bool {
             if constexpr (MX) return mx_update(p, s, k, wsm());
@@ -1706,6 +1744,7 @@ struct bddc_handle {
     double bytes_iter = 0.0, bytes_pre = 0.0, bytes_post = 0.0;
     mutable std::vector<double> hist_a, hist_b;  // host copies of the CG coefficients
     bddc_tuning tuning{};                        // work layout of the solve launch
+    std::vector<int2> dunit_h;                   // operator-apply units (host copy, for the warp ranges)
 };
 
 // message of the last failed setup of this thread (bddc_last_error(NULL));
@@ -1892,6 +1931,49 @@ std::vector<int64_t> warp_ranges(const Packed& P, int64_t NS, int64_t W, double 
     return ws;
 }
 
+// operator-apply units: every subdomain in J = ceil(n_Gamma^2 /
+// kDiropPartCost) parts of consecutive outputs (one part in the full-space
+// form, whose operator is not a square block); a part's outputs are
+// [ob, oe), packed as (ob << 16) | oe
+void dirop_units(const Packed& P, int n_inst, bool full, std::vector<int2>& du, std::vector<int64_t>& sub_du0,
+                 std::vector<int64_t>& inst_du0) {
+    const int64_t NS = (int64_t)P.sub_ng.size();
+    du.clear();
+    sub_du0.assign(NS + 1, 0);
+    for (int64_t s = 0; s < NS; ++s) {
+        const int ng = P.sub_ng[s];
+        const int64_t cost = (int64_t)ng * ng;
+        const int J = full ? 1 : (int)std::max<int64_t>(1, (cost + kDiropPartCost - 1) / kDiropPartCost);
+        for (int j = 0; j < J; ++j) {
+            const int ob = (int)(((int64_t)ng * j) / J), oe = (int)(((int64_t)ng * (j + 1)) / J);
+            du.push_back(make_int2((int)s, (ob << 16) | oe));
+        }
+        sub_du0[s + 1] = (int64_t)du.size();
+    }
+    inst_du0.assign(n_inst + 1, 0);
+    for (int b = 0; b < n_inst; ++b) inst_du0[b + 1] = sub_du0[P.inst_s1[b]];
+}
+
+// contiguous operator-apply unit ranges of W warps at equal fractions of the
+// summed cost (outputs x n_Gamma + C); W + 1 entries
+std::vector<int64_t> dirop_ranges(const Packed& P, const std::vector<int2>& du, int64_t W, double C) {
+    const int64_t NU = (int64_t)du.size();
+    std::vector<double> pre(NU + 1, 0.0);
+    for (int64_t u = 0; u < NU; ++u) {
+        const int ob = du[u].y >> 16, oe = du[u].y & 0xffff;
+        pre[u + 1] = pre[u] + (double)(oe - ob) * P.sub_ng[du[u].x] + C;
+    }
+    std::vector<int64_t> ws(W + 1);
+    int64_t u = 0;
+    for (int64_t w = 0; w < W; ++w) {
+        const double target = pre[NU] * (double)w / (double)W;
+        while (u < NU && pre[u] < target) ++u;
+        ws[w] = u;
+    }
+    ws[W] = NU;
+    return ws;
+}
+
 // launch grid of the persistent kernel: one CTA per subdomain or coarse unit,
 // at most the resident CTAs of the device
 int solve_grid(int nb, int nsm, int64_t n_sub, int64_t n_cunits) {
@@ -1998,7 +2080,10 @@ int autotune_layout(bddc_handle* h, int64_t* ws_dev, int* cu_inst_dev, int* cu_r
     };
     auto set_weight = [&](double C) -> bool {
         const std::vector<int64_t> ws = warp_ranges(P, NS, W, C);
-        return cudaMemcpy(ws_dev, ws.data(), ws.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+        const std::vector<int64_t> wu = dirop_ranges(P, h->dunit_h, W, C);
+        return cudaMemcpy(ws_dev, ws.data(), ws.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(const_cast<int64_t*>(p.warp_du0), wu.data(), wu.size() * sizeof(int64_t),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -2089,6 +2174,15 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     std::vector<int> cu_inst, cu_row0;
     std::vector<int64_t> cu0;
     coarse_units(P, n_instances, opt.autotune ? 8 : kCoarseRows, cu_inst, cu_row0, cu0);
+    // operator-apply units (a part's output range is packed in 16 bits)
+    if (P.max_ng > 0xffff) {
+        bddc_destroy(h);
+        return BDDC_E_INVALID_ARG;
+    }
+    std::vector<int2> du;
+    std::vector<int64_t> sub_du0, inst_du0;
+    dirop_units(P, n_instances, opt.formulation == BDDC_FORM_FULL, du, sub_du0, inst_du0);
+    h->dunit_h = du;
     h->inst_cfoff.assign(n_instances, 0);
     for (int b = 1; b < n_instances; ++b) h->inst_cfoff[b] = h->inst_cfoff[b - 1] + P.inst_ncf[b - 1];
     Params& p = h->prm;
@@ -2106,6 +2200,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     UP(slot_dsig, P.slot_dsig); UP(cslot_c, P.cslot_c); UP(cell_gid, P.cell_gid); UP(int_fid, P.int_fid);
     UP(g_fid, P.g_fid); UP(g_bsign, P.g_bsign); UP(c_slot_a, P.c_slot_a); UP(c_slot_b, P.c_slot_b);
     UP(cunit_inst, cu_inst); UP(cunit_row0, cu_row0); UP(inst_cu0, cu0);
+    UP(dunit, du); UP(sub_du0, sub_du0); UP(inst_du0, inst_du0);
     if (opt.formulation == BDDC_FORM_FULL) {
         UP(slot_fk, P.slot_fk); UP(slot_fopp, P.slot_fopp); UP(slot_fcell, P.slot_fcell);
     }
@@ -2286,7 +2381,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     AL(ql, L); AL(zl, L); AL(yl, L); AL(rl, L); AL(tl, L);
     AL(rcl, CL); AL(wc, P.n_coarse_vec);
     AL(xp, NS); AL(dp0, NS); AL(dp1, NS); AL(zp, NS); AL(prhs, NS);
-    AL(part_dq, NS); AL(part_rr, NS); AL(part_rz, NS); AL(part_a1, NS); AL(part_a2, NS);
+    AL(part_dq, (int64_t)du.size()); AL(part_rr, NS); AL(part_rz, NS); AL(part_a1, NS); AL(part_a2, NS);
     AL(inst_cnt, (size_t)n_instances * kCounters); AL(inst_tot, (size_t)n_instances * kTotals);
     AL(st, n_instances); AL(alpha_hist, H); AL(beta_hist, H); AL(rho_hist, H);
     AL(n_active, 1); AL(gsync, 1);
@@ -2303,6 +2398,7 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
     }
     p.n_inst = n_instances;
     p.n_sub = NS;
+    p.n_du = (int64_t)du.size();
     if (opt.autotune) coarse_units(P, n_instances, kCoarseRows, cu_inst, cu_row0, cu0);
     if (!cu_inst.empty() && opt.autotune) {  // the default units into the larger buffers
         cudaMemcpy(const_cast<int*>(p.cunit_inst), cu_inst.data(), cu_inst.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -2353,11 +2449,14 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
         // subdomain counts; pure n_Gamma^2 made the regular partitions
         // 3-13 % slower, this weight within 1 %.
         const int64_t* d = nullptr;
-        if (upload(h, warp_ranges(P, NS, (int64_t)h->grid * kWarps, kBalanceWeight), &d) != BDDC_OK) {
+        const int64_t* dd = nullptr;
+        if (upload(h, warp_ranges(P, NS, (int64_t)h->grid * kWarps, kBalanceWeight), &d) != BDDC_OK ||
+            upload(h, dirop_ranges(P, h->dunit_h, (int64_t)h->grid * kWarps, kBalanceWeight), &dd) != BDDC_OK) {
             bddc_destroy(h);
             return BDDC_E_OOM;
         }
         p.warp_sub0 = d;
+        p.warp_du0 = dd;
     }
     h->tuning.balance_weight = kBalanceWeight;
     h->tuning.coarse_rows = kCoarseRows;
@@ -2602,7 +2701,7 @@ int bddc_debug_vector(const bddc_handle* h, const char* name, double* dst, int64
     else if (n == "prhs") { src = p.prhs; len = NS; }
     else if (n == "part_rr") { src = p.part_rr; len = NS; }
     else if (n == "part_rz") { src = p.part_rz; len = NS; }
-    else if (n == "part_dq") { src = p.part_dq; len = NS; }
+    else if (n == "part_dq") { src = p.part_dq; len = p.n_du; }
     else if (n == "alpha") { src = p.alpha_hist; len = (int64_t)h->n_inst * (p.maxit + 1); }
     else if (n == "beta") { src = p.beta_hist; len = (int64_t)h->n_inst * (p.maxit + 1); }
     else return BDDC_E_INVALID_ARG;

@@ -30,6 +30,7 @@ namespace bddc {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCoarseRows = 16;             // coarse rows per work unit (default; Params::coarse_rows)
+constexpr int64_t kDiropPartCost = 32768;    // largest n_out x n_Gamma of one operator-apply unit
 constexpr long long kBarrierWaitNs = 10000000000LL;  // a grid-barrier wait past 10 s is an error
 constexpr int kActMaxInst = 4096;           // largest batch whose CG phases are rebalanced over active instances
 
@@ -87,6 +88,15 @@ struct Params {
     // subdomains
     int64_t n_sub;
     const int64_t* warp_sub0;  // per warp of the solve launch: first subdomain of its range (warps + 1)
+    // operator-apply units: a subdomain whose S^i block exceeds kDiropPartCost
+    // entries is applied in parts, each a range of its outputs (dunit[u]:
+    // subdomain, (first output << 16) | end output), so that no part is
+    // longer than a warp's share of the phase; units of a subdomain are
+    // consecutive, sub_du0 (n_sub + 1) and inst_du0 (n_inst + 1) their first
+    const int2* dunit;
+    const int64_t *sub_du0, *inst_du0;
+    const int64_t* warp_du0;  // per warp: first unit of its range (warps + 1)
+    int64_t n_du;
     const int *sub_inst, *sub_ng, *sub_ni, *sub_nc, *sub_m, *sub_local;
     const int64_t *off_S, *off_F, *off_P, *off_Gpre, *off_Gpost, *off_slot, *off_cslot, *off_cell, *off_int;
     const double* sub_d;
@@ -128,7 +138,7 @@ struct Params {
     double* rcl;                                               // coarse slots
     double* wc;                                                // coarse vectors
     double *xp, *dp0, *dp1, *zp, *prhs;                        // per subdomain
-    double *part_dq, *part_rr, *part_rz, *part_a1, *part_a2;   // per subdomain partials
+    double *part_dq, *part_rr, *part_rz, *part_a1, *part_a2;   // per subdomain partials (part_dq: per operator-apply unit)
     int* inst_cnt;      // per instance and partial kind: arrivals of subdomain partials
     double* inst_tot;   // per instance: totals of the partials (rr, rz, dq, a1, a2)
     InstState* st;

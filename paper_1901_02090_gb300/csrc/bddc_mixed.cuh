@@ -294,8 +294,10 @@ __device__ bool mx_prolong(const Params& p, int64_t s, WarpSm w) {
     return true;
 }
 
-// direction update and operator apply (pairs)
-__device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm w) {
+// direction update and operator apply (pairs), for the outputs [ob, oe) of
+// operator-apply unit u of subdomain s (the unit with ob = 0 also stores
+// the subdomain's new direction)
+__device__ bool mx_dirop(const Params& p, int64_t u, int64_t s, int ob, int oe, int k, WarpSm w) {
     const int b = p.sub_inst[s];
     if (inst_done(p, b)) return false;
     const int l = threadIdx.x & 31;
@@ -314,24 +316,24 @@ __device__ bool mx_dirop(const Params& p, int64_t s, int k, WarpSm w) {
         float2 z = __ldcg(zl + so + kk);
         if (pt >= 0) z = dd_add(z, __ldcg(zl + pt));
         const float2 dn = (k == 0) ? z : dd_add(z, dd_mul(beta2, __ldcg(dold + gi)));
-        if (slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
+        if (ob == 0 && slot_owner((int)(so + kk), pt)) dnew[gi] = dn;
         w.xh[kk] = dn.x;
         w.xl[kk] = dn.y;
     }
     const double dpn = (k == 0) ? __ldcg(p.zp + s) : __ldcg(p.zp + s) + beta * __ldcg(dpold + s);
-    if (l == 0) dpnew[s] = dpn;
+    if (l == 0 && ob == 0) dpnew[s] = dpn;
     const float2 dpn2 = dd_of(dpn);
     __syncwarp();
     const float2* S = reinterpret_cast<const float2*>(p.S) + p.off_S[s];
     float2* ql = V2(p.ql);
     float2 dq = dd_zero();
-    gemv_warp(S, ng, w, [&](int kk, float2 y) {
+    gemv_warp_range(S, ng, ob, oe, w, [&](int kk, float2 y) {
         const float2 q = dd_add(y, dd_mul(__ldg(p.slot_dsig2 + so + kk), dpn2));
         ql[so + kk] = q;
         dq = dd_add(dq, dd_mul(make_float2(w.xh[kk], w.xl[kk]), q));
     });
     dq = dd_warp_sum(dq);
-    if (l == 0) p.part_dq[s] = dd_dbl(dq);
+    if (l == 0) p.part_dq[u] = dd_dbl(dq);
     __syncwarp();
     return true;
 }
