@@ -275,9 +275,10 @@ __device__ __forceinline__ void warp_range(int64_t U, int64_t& a, int64_t& b) {
     b = (U * (w + 1)) / W;
 }
 // this warp's contiguous range of subdomains, balanced by work: the host
-// splits the subdomains at equal fractions of the summed cost n_Gamma^2 +
-// 4096 (S and F, plus the fixed latency of a unit), so a warp drawn several
-// large subdomains of an uneven partition does not set the length of a phase
+// splits the subdomains at equal fractions of the summed cost n_Gamma^2 + C
+// (S and F, plus the fixed latency C of a unit: 4096, or the autotuner's
+// choice), so a warp drawn several large subdomains of an uneven partition
+// does not set the length of a phase
 __device__ __forceinline__ void sub_range(const Params& p, int64_t& a, int64_t& b) {
     const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
     a = p.warp_sub0[w];
@@ -2418,8 +2419,13 @@ int setup_from_packed(int n_instances, const bddc_options& opt, void* cuda_strea
                                                                        2 * ((size_t)p.max_m + 1) + p.max_ext)) +
               sizeof(int) * 2 * ((size_t)p.act_n + 1);
     if (h->smem > 200 * 1024) {
+        // the CTA's dense coarse right-hand side plus 8 warp areas (each with
+        // the largest subdomain's interior fluxes and cells for the
+        // post-correction) must fit one CTA's shared memory
+        g_setup_err = "shared memory per CTA (" + std::to_string(h->smem / 1024) +
+                      " KB) above 200 KB: the dense coarse problem or a subdomain's interior is too large";
         bddc_destroy(h);
-        return BDDC_E_INVALID_ARG;  // coarse problem too large for the dense coarse solve
+        return BDDC_E_INVALID_ARG;
     }
     const void* kfn = solve_kernel_fn(opt.precision, opt.formulation, p.act_n > 1);
     // the stand-alone operator / preconditioner kernels use the same carve

@@ -468,3 +468,49 @@ def test_autotuned_layout_is_bitwise_equal_and_cached(bddc, kind, precision):
         assert np.array_equal(out[2], heur[2])
         assert np.array_equal(out[0], heur[0])
         assert np.array_equal(out[1], heur[1])
+
+
+def _split_cases():
+    """Subdomains whose S^i exceeds the 32768 entries of one operator-apply
+    unit: 8^3-cell boxes (n_Gamma up to 256: three inner faces and a
+    pressure face) of a layered 3D field, and seeded boxes of 3-8 cells per
+    axis on a 24 x 20 x 16 grid (36 subdomains, 12 of them above the limit,
+    n_Gamma up to 287; the c4 partition's shape at a size the oracle takes).
+    (2D subdomains that large do not fit the kernel's shared-memory areas.)"""
+    from synth.problems import layered_3d
+    g3 = Grid(3, (16, 16, 16), (20.0, 10.0, 2.0))
+    t3, v3 = pressure_drop_bc(g3)
+    p3 = Problem("split3d", g3, layered_3d(g3, 77), box_partition(g3, (2, 2, 2)).astype(np.int32), t3, v3,
+                 np.zeros(g3.n_cells))
+    gi = Grid(3, (24, 20, 16), (20.0, 10.0, 2.0))
+    ti, vi = pressure_drop_bc(gi)
+    pi = Problem("split_irr3d", gi, layered_3d(gi, 4085), irregular_box_partition(gi, 4085).astype(np.int32),
+                 ti, vi, np.zeros(gi.n_cells))
+    return p3, pi
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_operator_apply_in_parts_matches_oracle(bddc, which):
+    """Subdomains applied as several operator-apply units (their S^i rows in
+    output ranges on several warps, the (d, q) partials summed in unit
+    order): FP64 and mixed against the oracle, and, in a batch with a small
+    instance (the rebalancing kernel), bitwise equal to the solo solve."""
+    pb = _split_cases()[which]
+    hs = bddc.HostSetup([pb], bddc.default_options(tau=4.0))
+    ng = hs.get("sub_ng")
+    hs.close()
+    assert int((ng.astype(np.int64) ** 2).max()) > 32768
+    o = BDDCOracle(pb, tau=4.0)
+    ref = o.solve(tol=1e-8)
+    flux, pres, its, st, _ = gpu_solve(bddc, [pb], 1e-8, 4.0)
+    assert abs(int(its[0]) - ref.iterations) <= iteration_slack(ref.iterations, ref.kappa)
+    assert _rel(flux, ref.flux) <= FP64_REL * max(1.0, ref.kappa)
+    assert _rel(pres, ref.pressure) <= FP64_REL * max(1.0, ref.kappa)
+    f32, p32, i32, _, _ = gpu_solve(bddc, [pb], 1e-8, 4.0, precision=bddc.BDDC_PREC_FP32)
+    assert _rel(f32, ref.flux) <= MIXED_REL and _rel(p32, ref.pressure) <= MIXED_REL
+    for prec, (fa, pa, ia) in ((0, (flux, pres, its)), (1, (f32, p32, i32))):
+        pbs = [pb, make_config("c1")]
+        fb, pbv, ib, _, _ = gpu_solve(bddc, pbs, 1e-8, 4.0, precision=prec)
+        assert ib[0] == ia[0]
+        assert np.array_equal(fb[:len(fa)], fa)
+        assert np.array_equal(pbv[:len(pa)], pa)
