@@ -15,8 +15,10 @@
 //   k_fe_inverse  one CTA per subdomain: (S^i)^{-1} in place by Gauss-Jordan
 //                 elimination (S^i is SPD, so no pivoting), which turns the
 //                 T blocks of all of a subdomain's faces into gathers;
-//   k_fe_face     one thread per face: the O(f^3) dense steps above, on a
-//                 per-face slice of global scratch.
+//   k_fe_face     one warp per face: the O(f^3) dense steps above, on a
+//                 per-face slice of global scratch, each element of a step
+//                 on one lane in the order of the sequential loop (the
+//                 results do not depend on the lane count).
 // The host keeps the last step (orthonormalising the rows against the
 // face's existing constraint rows) and everything around it.
 #include <cuda_runtime.h>
@@ -97,27 +99,38 @@ __global__ void __launch_bounds__(kFeThreads) k_fe_inverse(FeView v) {
     if (threadIdx.x == 0) v.sub_status[s] = bad ? BDDC_E_SETUP : BDDC_OK;
 }
 
-// ---- small dense FP64 routines of one thread (row-major) ----------------------------
-__device__ bool fe_chol(int n, double* A) {
+// ---- dense FP64 routines of one warp (row-major) ------------------------------------
+// One warp per face.  Every output element is computed by one lane with the
+// operations in the order of a sequential loop over the element's terms, so
+// the results do not depend on how the elements are spread over the lanes;
+// __syncwarp separates dependent steps.  Branch conditions are computed by
+// every lane from the same values, so the warp stays converged.
+
+// A = L L^T in place (L in the lower triangle, zeros above); false when A
+// is not positive definite
+__device__ bool fw_chol(int n, double* A) {
+    const int l = threadIdx.x & 31;
     for (int j = 0; j < n; ++j) {
         double s = A[(int64_t)j * n + j];
         for (int k = 0; k < j; ++k) s -= A[(int64_t)j * n + k] * A[(int64_t)j * n + k];
         if (!(s > 0.0)) return false;
         const double d = sqrt(s);
-        A[(int64_t)j * n + j] = d;
-        for (int i = j + 1; i < n; ++i) {
+        __syncwarp();
+        for (int i = j + 1 + l; i < n; i += 32) {
             double t = A[(int64_t)i * n + j];
             for (int k = 0; k < j; ++k) t -= A[(int64_t)i * n + k] * A[(int64_t)j * n + k];
             A[(int64_t)i * n + j] = t / d;
         }
-        for (int k = j + 1; k < n; ++k) A[(int64_t)j * n + k] = 0.0;
+        for (int k = j + 1 + l; k < n; k += 32) A[(int64_t)j * n + k] = 0.0;
+        if (l == 0) A[(int64_t)j * n + j] = d;
+        __syncwarp();
     }
     return true;
 }
 
-// B <- A^{-1} B with the Cholesky factor L (A = L L^T), B n x m
-__device__ void fe_chol_solve(int n, const double* L, double* B, int m) {
-    for (int c = 0; c < m; ++c) {
+// B <- A^{-1} B with the Cholesky factor L (A = L L^T), B n x m; a lane per column
+__device__ void fw_chol_solve(int n, const double* L, double* B, int m) {
+    for (int c = threadIdx.x & 31; c < m; c += 32) {
         for (int i = 0; i < n; ++i) {
             double v = B[(int64_t)i * m + c];
             for (int k = 0; k < i; ++k) v -= L[(int64_t)i * n + k] * B[(int64_t)k * m + c];
@@ -129,13 +142,17 @@ __device__ void fe_chol_solve(int n, const double* L, double* B, int m) {
             B[(int64_t)i * m + c] = v / L[(int64_t)i * n + i];
         }
     }
+    __syncwarp();
 }
 
 // cyclic Jacobi eigensolver of a symmetric n x n A (destroyed): eigenvalues
-// in w, eigenvectors as the columns of V
-__device__ void fe_jacobi(int n, double* A, double* w, double* V) {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) V[(int64_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+// in w, eigenvectors as the columns of V.  The rotations run in the cyclic
+// order; each one updates its two columns, then its two rows, then V, with
+// a lane per index k.
+__device__ void fw_jacobi(int n, double* A, double* w, double* V) {
+    const int l = threadIdx.x & 31;
+    for (int q = l; q < n * n; q += 32) V[q] = (q / n == q % n) ? 1.0 : 0.0;
+    __syncwarp();
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0.0, tot = 0.0;
         for (int i = 0; i < n; ++i)
@@ -153,30 +170,35 @@ __device__ void fe_jacobi(int n, double* A, double* w, double* V) {
                 const double theta = (aqq - app) / (2.0 * apq);
                 const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                 const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {
+                __syncwarp();
+                for (int k = l; k < n; k += 32) {
                     const double akp = A[(int64_t)k * n + p], akq = A[(int64_t)k * n + q];
                     A[(int64_t)k * n + p] = c * akp - s * akq;
                     A[(int64_t)k * n + q] = s * akp + c * akq;
                 }
-                for (int k = 0; k < n; ++k) {
+                __syncwarp();
+                for (int k = l; k < n; k += 32) {
                     const double apk = A[(int64_t)p * n + k], aqk = A[(int64_t)q * n + k];
                     A[(int64_t)p * n + k] = c * apk - s * aqk;
                     A[(int64_t)q * n + k] = s * apk + c * aqk;
                 }
-                for (int k = 0; k < n; ++k) {
+                for (int k = l; k < n; k += 32) {
                     const double vkp = V[(int64_t)k * n + p], vkq = V[(int64_t)k * n + q];
                     V[(int64_t)k * n + p] = c * vkp - s * vkq;
                     V[(int64_t)k * n + q] = s * vkp + c * vkq;
                 }
+                __syncwarp();
             }
     }
-    for (int i = 0; i < n; ++i) w[i] = A[(int64_t)i * n + i];
+    for (int i = l; i < n; i += 32) w[i] = A[(int64_t)i * n + i];
+    __syncwarp();
 }
 
-// the face-reduced pair eigenproblem of one face (one thread)
+// the face-reduced pair eigenproblem of one face (one warp)
 __global__ void __launch_bounds__(kFeThreads) k_fe_face(FeView v) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= v.nface) return;
+    const int t = blockIdx.x * (kFeThreads / 32) + (threadIdx.x >> 5);
+    if (t >= v.nface) return;  // whole warp
+    const int l = threadIdx.x & 31;
     const int si = v.fi[t], sj = v.fj[t], f = v.ff[t];
     const int ni = v.n[si], nj = v.n[sj];
     const int* pi = v.pi + v.o_f[t];
@@ -186,9 +208,11 @@ __global__ void __launch_bounds__(kFeThreads) k_fe_face(FeView v) {
     const double *Si = v.S + v.o_S[si], *Sj = v.S + v.o_S[sj];
     const double *wi = v.w + v.o_w[si], *wj = v.w + v.o_w[sj];
     double* out_rows = v.rows + v.o_rows[t];
-    v.omega[t] = 0.0;
-    v.nrows[t] = 0;
-    v.face_status[t] = BDDC_OK;
+    if (l == 0) {
+        v.omega[t] = 0.0;
+        v.nrows[t] = 0;
+        v.face_status[t] = BDDC_OK;
+    }
     // scratch slices (f x f unless noted)
     double* base = v.scr + v.o_scr[t];
     const int64_t ff = (int64_t)f * f;
@@ -196,160 +220,201 @@ __global__ void __launch_bounds__(kFeThreads) k_fe_face(FeView v) {
            *M = Br + ff, *V = M + ff, *Z = V + ff, *vec = Z + ff;  // vec: 6 f
     double *lam = vec, *cm = vec + f, *hv = vec + 3 * f, *eta = vec + 4 * f, *delta = vec + 5 * f;
     // G = sym(T_i) + sym(T_j), S_F = w_j S^i_ff w_j + w_i S^j_ff w_i
-    for (int a = 0; a < f; ++a)
-        for (int b = 0; b < f; ++b) {
-            const double tia = Ii[(int64_t)pi[a] * ni + pi[b]], tib = Ii[(int64_t)pi[b] * ni + pi[a]];
-            const double tja = Ij[(int64_t)pj[a] * nj + pj[b]], tjb = Ij[(int64_t)pj[b] * nj + pj[a]];
-            G[(int64_t)a * f + b] = 0.5 * (tia + tib) + 0.5 * (tja + tjb);
-            SF[(int64_t)a * f + b] = wj[pj[a]] * Si[(int64_t)pi[a] * ni + pi[b]] * wj[pj[b]] +
-                                     wi[pi[a]] * Sj[(int64_t)pj[a] * nj + pj[b]] * wi[pi[b]];
-        }
+    for (int64_t e = l; e < ff; e += 32) {
+        const int a = (int)(e / f), b = (int)(e % f);
+        const double tia = Ii[(int64_t)pi[a] * ni + pi[b]], tib = Ii[(int64_t)pi[b] * ni + pi[a]];
+        const double tja = Ij[(int64_t)pj[a] * nj + pj[b]], tjb = Ij[(int64_t)pj[b] * nj + pj[a]];
+        G[e] = 0.5 * (tia + tib) + 0.5 * (tja + tjb);
+        SF[e] = wj[pj[a]] * Si[(int64_t)pi[a] * ni + pi[b]] * wj[pj[b]] +
+                wi[pi[a]] * Sj[(int64_t)pj[a] * nj + pj[b]] * wi[pi[b]];
+    }
     // the face's net-flux rows on the jump, c o w_j and c o w_i, orthonormalised
-    // (the second dropped when it is (nearly) parallel to the first)
+    // (the second dropped when it is (nearly) parallel to the first): lane 0
     int r = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        double* row = cm + (int64_t)r * f;
-        double n0 = 0.0;
-        for (int q = 0; q < f; ++q) {
-            row[q] = cf[q] * (pass == 0 ? wj[pj[q]] : wi[pi[q]]);
-            n0 += row[q] * row[q];
-        }
-        n0 = sqrt(n0);
-        for (int rep = 0; rep < 2; ++rep)
-            for (int b = 0; b < r; ++b) {
-                double dot = 0.0;
-                for (int q = 0; q < f; ++q) dot += cm[(int64_t)b * f + q] * row[q];
-                for (int q = 0; q < f; ++q) row[q] -= dot * cm[(int64_t)b * f + q];
+    if (l == 0) {
+        for (int pass = 0; pass < 2; ++pass) {
+            double* row = cm + (int64_t)r * f;
+            double n0 = 0.0;
+            for (int q = 0; q < f; ++q) {
+                row[q] = cf[q] * (pass == 0 ? wj[pj[q]] : wi[pi[q]]);
+                n0 += row[q] * row[q];
             }
-        double nn = 0.0;
-        for (int q = 0; q < f; ++q) nn += row[q] * row[q];
-        nn = sqrt(nn);
-        if (n0 > 0 && nn > 1e-10 * n0) {
-            for (int q = 0; q < f; ++q) row[q] /= nn;
-            ++r;
+            n0 = sqrt(n0);
+            for (int rep = 0; rep < 2; ++rep)
+                for (int b = 0; b < r; ++b) {
+                    double dot = 0.0;
+                    for (int q = 0; q < f; ++q) dot += cm[(int64_t)b * f + q] * row[q];
+                    for (int q = 0; q < f; ++q) row[q] -= dot * cm[(int64_t)b * f + q];
+                }
+            double nn = 0.0;
+            for (int q = 0; q < f; ++q) nn += row[q] * row[q];
+            nn = sqrt(nn);
+            if (n0 > 0 && nn > 1e-10 * n0) {
+                for (int q = 0; q < f; ++q) row[q] /= nn;
+                ++r;
+            }
         }
     }
+    r = __shfl_sync(0xffffffffu, r, 0);
     const int nz = f - r;
-    if (nz <= 0) return;
+    if (nz <= 0) return;  // whole warp
     // Z: the last f - r columns of Q of the Householder QR of C^T (f x r)
-    for (int i = 0; i < f; ++i)
-        for (int j = 0; j < f; ++j) Q[(int64_t)i * f + j] = (i == j) ? 1.0 : 0.0;
+    for (int64_t e = l; e < ff; e += 32) Q[e] = (e / f == e % f) ? 1.0 : 0.0;
+    __syncwarp();
     // R = C^T kept in Lg (f x r)
-    for (int i = 0; i < r; ++i)
-        for (int j = 0; j < f; ++j) Lg[(int64_t)j * r + i] = cm[(int64_t)i * f + j];
+    for (int e = l; e < r * f; e += 32) {
+        const int i = e / f, j = e % f;
+        Lg[(int64_t)j * r + i] = cm[(int64_t)i * f + j];
+    }
+    __syncwarp();
     for (int k = 0; k < r && k < f; ++k) {
-        double nrm = 0.0;
-        for (int i = k; i < f; ++i) nrm += Lg[(int64_t)i * r + k] * Lg[(int64_t)i * r + k];
-        nrm = sqrt(nrm);
-        if (nrm == 0.0) continue;
-        const double x0 = Lg[(int64_t)k * r + k];
-        const double alpha = x0 > 0 ? -nrm : nrm;
-        for (int i = 0; i < f; ++i) hv[i] = 0.0;
-        hv[k] = x0 - alpha;
-        for (int i = k + 1; i < f; ++i) hv[i] = Lg[(int64_t)i * r + k];
-        double vv = 0.0;
-        for (int i = k; i < f; ++i) vv += hv[i] * hv[i];
-        if (vv == 0.0) continue;
-        const double beta = 2.0 / vv;
-        for (int c = k; c < r; ++c) {
-            double s = 0.0;
-            for (int i = k; i < f; ++i) s += hv[i] * Lg[(int64_t)i * r + c];
-            s *= beta;
-            for (int i = k; i < f; ++i) Lg[(int64_t)i * r + c] -= s * hv[i];
+        // the reflector and the update of R on lane 0; then Q's rows, a lane per row
+        double beta = 0.0;
+        if (l == 0) {
+            double nrm = 0.0;
+            for (int i = k; i < f; ++i) nrm += Lg[(int64_t)i * r + k] * Lg[(int64_t)i * r + k];
+            nrm = sqrt(nrm);
+            if (nrm != 0.0) {
+                const double x0 = Lg[(int64_t)k * r + k];
+                const double alpha = x0 > 0 ? -nrm : nrm;
+                for (int i = 0; i < f; ++i) hv[i] = 0.0;
+                hv[k] = x0 - alpha;
+                for (int i = k + 1; i < f; ++i) hv[i] = Lg[(int64_t)i * r + k];
+                double vv = 0.0;
+                for (int i = k; i < f; ++i) vv += hv[i] * hv[i];
+                if (vv != 0.0) {
+                    beta = 2.0 / vv;
+                    for (int c = k; c < r; ++c) {
+                        double s = 0.0;
+                        for (int i = k; i < f; ++i) s += hv[i] * Lg[(int64_t)i * r + c];
+                        s *= beta;
+                        for (int i = k; i < f; ++i) Lg[(int64_t)i * r + c] -= s * hv[i];
+                    }
+                }
+            }
         }
-        for (int rr = 0; rr < f; ++rr) {
+        beta = __shfl_sync(0xffffffffu, beta, 0);
+        __syncwarp();
+        if (beta == 0.0) continue;  // a zero column or reflector: no update (whole warp)
+        for (int rr = l; rr < f; rr += 32) {
             double s = 0.0;
             for (int i = k; i < f; ++i) s += Q[(int64_t)rr * f + i] * hv[i];
             s *= beta;
             for (int i = k; i < f; ++i) Q[(int64_t)rr * f + i] -= s * hv[i];
         }
+        __syncwarp();
     }
-    for (int a = 0; a < f; ++a)
-        for (int c = 0; c < nz; ++c) Z[(int64_t)a * nz + c] = Q[(int64_t)a * f + r + c];
+    for (int e = l; e < f * nz; e += 32) {
+        const int a = e / nz, c = e % nz;
+        Z[e] = Q[(int64_t)a * f + r + c];
+    }
     // A_r = Z^T S_F Z, B_r = Z^T G^{-1} Z
-    for (int64_t q = 0; q < ff; ++q) Lg[q] = G[q];
-    if (!fe_chol(f, Lg)) return;  // omega 0, no rows: as on the host
-    for (int64_t q = 0; q < (int64_t)f * nz; ++q) GiZ[q] = Z[q];
-    fe_chol_solve(f, Lg, GiZ, nz);
+    for (int64_t q = l; q < ff; q += 32) Lg[q] = G[q];
+    __syncwarp();
+    if (!fw_chol(f, Lg)) return;  // omega 0, no rows: as on the host
+    for (int64_t q = l; q < (int64_t)f * nz; q += 32) GiZ[q] = Z[q];
+    __syncwarp();
+    fw_chol_solve(f, Lg, GiZ, nz);
     double* SFZ = M;  // f x nz, until M is formed
-    for (int a = 0; a < f; ++a)
-        for (int c = 0; c < nz; ++c) {
-            double acc = 0.0;
-            for (int b = 0; b < f; ++b) acc += SF[(int64_t)a * f + b] * Z[(int64_t)b * nz + c];
-            SFZ[(int64_t)a * nz + c] = acc;
+    for (int e = l; e < f * nz; e += 32) {
+        const int a = e / nz, c = e % nz;
+        double acc = 0.0;
+        for (int b = 0; b < f; ++b) acc += SF[(int64_t)a * f + b] * Z[(int64_t)b * nz + c];
+        SFZ[e] = acc;
+    }
+    __syncwarp();
+    for (int e = l; e < nz * nz; e += 32) {
+        const int x = e / nz, y = e % nz;
+        double sa = 0.0, sb = 0.0;
+        for (int a = 0; a < f; ++a) {
+            sa += Z[(int64_t)a * nz + x] * SFZ[(int64_t)a * nz + y];
+            sb += Z[(int64_t)a * nz + x] * GiZ[(int64_t)a * nz + y];
         }
-    for (int x = 0; x < nz; ++x)
-        for (int y = 0; y < nz; ++y) {
-            double sa = 0.0, sb = 0.0;
-            for (int a = 0; a < f; ++a) {
-                sa += Z[(int64_t)a * nz + x] * SFZ[(int64_t)a * nz + y];
-                sb += Z[(int64_t)a * nz + x] * GiZ[(int64_t)a * nz + y];
-            }
-            Ar[(int64_t)x * nz + y] = sa;
-            Br[(int64_t)x * nz + y] = sb;
-        }
-    for (int x = 0; x < nz; ++x)
-        for (int y = x + 1; y < nz; ++y) {
-            const double b = 0.5 * (Br[(int64_t)x * nz + y] + Br[(int64_t)y * nz + x]);
-            const double a = 0.5 * (Ar[(int64_t)x * nz + y] + Ar[(int64_t)y * nz + x]);
-            Br[(int64_t)x * nz + y] = Br[(int64_t)y * nz + x] = b;
-            Ar[(int64_t)x * nz + y] = Ar[(int64_t)y * nz + x] = a;
-        }
-    if (!fe_chol(nz, Br)) return;
-    // M = L^{-1} A_r L^{-T}
-    for (int64_t q = 0; q < (int64_t)nz * nz; ++q) M[q] = Ar[q];
-    for (int c = 0; c < nz; ++c)
+        Ar[e] = sa;
+        Br[e] = sb;
+    }
+    __syncwarp();
+    for (int e = l; e < nz * nz; e += 32) {
+        const int x = e / nz, y = e % nz;
+        if (y <= x) continue;
+        const double b = 0.5 * (Br[(int64_t)x * nz + y] + Br[(int64_t)y * nz + x]);
+        const double a = 0.5 * (Ar[(int64_t)x * nz + y] + Ar[(int64_t)y * nz + x]);
+        Br[(int64_t)x * nz + y] = Br[(int64_t)y * nz + x] = b;
+        Ar[(int64_t)x * nz + y] = Ar[(int64_t)y * nz + x] = a;
+    }
+    __syncwarp();
+    if (!fw_chol(nz, Br)) return;
+    // M = L^{-1} A_r L^{-T}: a lane per column, then a lane per row
+    for (int64_t q = l; q < (int64_t)nz * nz; q += 32) M[q] = Ar[q];
+    __syncwarp();
+    for (int c = l; c < nz; c += 32)
         for (int i = 0; i < nz; ++i) {
             double x = M[(int64_t)i * nz + c];
             for (int k = 0; k < i; ++k) x -= Br[(int64_t)i * nz + k] * M[(int64_t)k * nz + c];
             M[(int64_t)i * nz + c] = x / Br[(int64_t)i * nz + i];
         }
-    for (int rr = 0; rr < nz; ++rr)
+    __syncwarp();
+    for (int rr = l; rr < nz; rr += 32)
         for (int i = 0; i < nz; ++i) {
             double x = M[(int64_t)rr * nz + i];
             for (int k = 0; k < i; ++k) x -= Br[(int64_t)i * nz + k] * M[(int64_t)rr * nz + k];
             M[(int64_t)rr * nz + i] = x / Br[(int64_t)i * nz + i];
         }
-    for (int x = 0; x < nz; ++x)
-        for (int y = x + 1; y < nz; ++y)
-            M[(int64_t)x * nz + y] = M[(int64_t)y * nz + x] = 0.5 * (M[(int64_t)x * nz + y] + M[(int64_t)y * nz + x]);
-    fe_jacobi(nz, M, lam, V);
-    // eigenvalues in descending order (selection: stable, ties by index)
-    int* idx = reinterpret_cast<int*>(Ar);  // A_r is no longer needed
-    for (int q = 0; q < nz; ++q) idx[q] = q;
-    for (int a = 1; a < nz; ++a) {
-        const int key = idx[a];
-        int b = a - 1;
-        while (b >= 0 && lam[idx[b]] < lam[key]) {
-            idx[b + 1] = idx[b];
-            --b;
-        }
-        idx[b + 1] = key;
+    __syncwarp();
+    for (int e = l; e < nz * nz; e += 32) {
+        const int x = e / nz, y = e % nz;
+        if (y <= x) continue;
+        M[(int64_t)x * nz + y] = M[(int64_t)y * nz + x] = 0.5 * (M[(int64_t)x * nz + y] + M[(int64_t)y * nz + x]);
     }
+    __syncwarp();
+    fw_jacobi(nz, M, lam, V);
+    // eigenvalues in descending order (selection: stable, ties by index), the
+    // count above tau and omega: lane 0
+    int* idx = reinterpret_cast<int*>(Ar);  // A_r is no longer needed
     int k = 0;
-    if (v.tau > 0 && isfinite(v.tau))
-        while (k < nz && lam[idx[k]] > v.tau) ++k;
-    v.omega[t] = k < nz ? fmax(lam[idx[k]], 0.0) : 0.0;
-    // rows S_F Z L^{-T} y for the k eigenvectors y above tau
-    for (int l = 0; l < k; ++l) {
-        for (int q = 0; q < nz; ++q) eta[q] = V[(int64_t)q * nz + idx[l]];
-        for (int i = nz - 1; i >= 0; --i) {
-            double x = eta[i];
-            for (int kk = i + 1; kk < nz; ++kk) x -= Br[(int64_t)kk * nz + i] * eta[kk];
-            eta[i] = x / Br[(int64_t)i * nz + i];
+    if (l == 0) {
+        for (int q = 0; q < nz; ++q) idx[q] = q;
+        for (int a = 1; a < nz; ++a) {
+            const int key = idx[a];
+            int b = a - 1;
+            while (b >= 0 && lam[idx[b]] < lam[key]) {
+                idx[b + 1] = idx[b];
+                --b;
+            }
+            idx[b + 1] = key;
         }
-        for (int a = 0; a < f; ++a) {
+        if (v.tau > 0 && isfinite(v.tau))
+            while (k < nz && lam[idx[k]] > v.tau) ++k;
+        v.omega[t] = k < nz ? fmax(lam[idx[k]], 0.0) : 0.0;
+    }
+    k = __shfl_sync(0xffffffffu, k, 0);
+    __syncwarp();
+    // rows S_F Z L^{-T} y for the k eigenvectors y above tau
+    for (int e = 0; e < k; ++e) {
+        const int col = idx[e];
+        for (int q = l; q < nz; q += 32) eta[q] = V[(int64_t)q * nz + col];
+        __syncwarp();
+        if (l == 0)
+            for (int i = nz - 1; i >= 0; --i) {
+                double x = eta[i];
+                for (int kk = i + 1; kk < nz; ++kk) x -= Br[(int64_t)kk * nz + i] * eta[kk];
+                eta[i] = x / Br[(int64_t)i * nz + i];
+            }
+        __syncwarp();
+        for (int a = l; a < f; a += 32) {
             double d = 0.0;
             for (int q = 0; q < nz; ++q) d += Z[(int64_t)a * nz + q] * eta[q];
             delta[a] = d;
         }
-        for (int a = 0; a < f; ++a) {
+        __syncwarp();
+        for (int a = l; a < f; a += 32) {
             double s = 0.0;
             for (int b = 0; b < f; ++b) s += SF[(int64_t)a * f + b] * delta[b];
-            out_rows[(int64_t)l * f + a] = s;
+            out_rows[(int64_t)e * f + a] = s;
         }
+        __syncwarp();
     }
-    v.nrows[t] = k;
+    if (l == 0) v.nrows[t] = k;
 }
 
 template <class T>
@@ -495,7 +560,7 @@ int face_eigen_device(FaceEigenBatch& B, std::string& err) {
         c.omega = d_omega + t0;
         c.nrows = d_nrows + t0;
         c.face_status = d_fst + t0;
-        k_fe_face<<<(c.nface + 127) / 128, 128>>>(c);
+        k_fe_face<<<(c.nface + kFeThreads / 32 - 1) / (kFeThreads / 32), kFeThreads>>>(c);
         const cudaError_t e = cudaDeviceSynchronize();
         cudaFree(d_oscr);
         if (e != cudaSuccess) {
