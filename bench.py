@@ -247,12 +247,31 @@ def _c3_shaped():
     return Problem("c3-shaped", g, layered_3d(g, 1901), box_partition(g, (4, 4, 3)), t, v, np.zeros(g.n_cells))
 
 
+def _serving_oracle_sample(tau, tol, max_requests, max_seconds):
+    """The oracle on the serving stream's requests (config 5), each with its
+    own setup, one after the other: up to max_requests or max_seconds."""
+    from synth.problems import serving_request
+    from oracle import BDDCOracle
+    t0, c0 = time.perf_counter(), time.process_time()
+    n, its = 0, []
+    while n < max_requests and time.perf_counter() - t0 < max_seconds:
+        o = BDDCOracle(serving_request(n), tau=tau)
+        its.append(o.solve(tol=tol).iterations)
+        n += 1
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return {"value": n / dt, "unit": "solves/s", "cores": round(cpu / dt, 2),
+            "mean_latency_ms": 1e3 * dt / n, "iterations_mean": float(np.mean(its)),
+            "sample": f"the first {n} requests of the serving stream (30-60 x 110-220 cells), each set up "
+                      f"and solved in turn (setup included), in {dt:.1f} s"}
+
+
 def cpu_baseline(tau, tol, min_seconds=10.0):
     """The oracle as it stands (NumPy/SciPy FP64, setup excluded) on the
-    host cores: one c2 field with all cores and with one BLAS thread, and a
-    c3-shaped block (48 subdomains of the 60x220x85 partition's 5^3 boxes)
-    whose rate is also extrapolated to the full 8976-subdomain c3 solve by
-    subdomain-iterations.  cores = CPU time over wall time of the sample."""
+    host cores: one c2 field with all cores and with one BLAS thread, the
+    c1 field, a c3-shaped block (48 subdomains of the 60x220x85 partition's
+    5^3 boxes) whose rate is also extrapolated to the full 8976-subdomain c3
+    solve by subdomain-iterations, and a sample of the serving stream with
+    each request's setup.  cores = CPU time over wall time of the sample."""
     from synth import make_config
     v, cores, n, dt, it0 = _oracle_rate(make_config("c2", seed=2090), tau, tol, min_seconds)
     one = _one_thread_rate(tau, tol, min_seconds)
@@ -267,6 +286,10 @@ def cpu_baseline(tau, tol, min_seconds=10.0):
                              "sample": f"{one[2]} solves of the same field with one BLAS/OpenMP thread"}
     else:
         out["one_thread"] = one
+    v1, cores1, n1, dt1, it1 = _oracle_rate(make_config("c1"), tau, tol, 2.0)
+    out["c1"] = {"value": v1, "unit": "solves/s", "cores": cores1, "iterations": it1,
+                 "sample": f"{n1} solves of the 16x16 field (4x4 subdomains) in {dt1:.1f} s, setup excluded"}
+    out["c5_sample"] = _serving_oracle_sample(tau, tol, max_requests=20, max_seconds=25.0)
     out["c3_shaped"] = {"value": v3, "unit": "solves/s", "cores": cores3, "iterations": it3,
                         "sample": f"{n3} solves of a 20x20x15 block of the 60x220x85 workload (4x4x3 "
                                   f"subdomains of 5^3, tau={tau:g}) in {dt3:.1f} s",
