@@ -23,6 +23,9 @@ bddc            local constrained saddle-point solves, the coarse basis and
 adaptive        the local generalized eigenproblems on pairs of adjacent
                 subdomains (Sec. 3.1 eqs. (eigenvalue-problem-local-matrix)),
                 Algorithm 3 and the indicator omega-tilde (eq. (indicator)).
+msmfem          the multiscale (MsMFEM-style) constraints of the comparison
+                in Sec. 5 (pair Darcy problems with sources +-w) and
+                caller-given constraint rows.
 
 Parity status of each function is stated in its docstring; every function
 here is pinned by the CPU tests in ``tests/test_oracle_*.py`` except where a
