@@ -277,10 +277,10 @@ int bddc_subassembled_apply(int n_sub, const int* ng, const int64_t* slot_offset
  *     BDDC_NOALLOC_MAX_SLOTS is rejected with BDDC_E_INVALID_ARG (message
  *     from bddc_last_error(NULL)); the kernels never address the array past
  *     slot_offset[n_sub], whatever the index tables hold;
- *   - the read-back synchronises `stream`, so the call cannot be captured in
- *     a CUDA graph;
+ *   - the read-back synchronises `stream` before the kernels are queued;
  *   - the first call on a device looks up the array's device address on the
- *     current device (once per device);
+ *     current device (once per device); make that first call before any
+ *     stream capture;
  *   - every call on a device shares the one array; it needs no clearing
  *     (each call writes every slot it reads), and calls whose kernels
  *     overlap on the GPU (different streams, or another host thread) race on
